@@ -1,0 +1,387 @@
+"""Benchmark of the single-pass ID hot path on the streamed channel-field workload.
+
+One step = one pass of the whole hot path over one snapshot matrix:
+reset -> stream the 1000 snapshots in chunks of 32 (both sketches and the
+coarse rows in one read of A) -> id_factor (pivoted QR of W, solve for P) ->
+id_coarse_factor (sub-sampled ID of A_c) -> id_reconstruct_error (A(:,J)P).
+
+Workload: 128 x 96 x 128 grid x 3 components (m = 4,718,592 rows) x 1000
+snapshots, FP32 (18.87 GB, larger than L2, resident in HBM), l = 60, k = 50,
+coarse grid 4x per direction.  Metric: GB/s of snapshot data per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: each rank compresses its own matrix (replicas, weak
+scaling, no collective on the data path).  ``--impl reference`` times the FP64
+oracle on the host cores on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "single-pass ID GB/s of snapshot data at fixed rel. error; % of HBM roofline"
+UNIT = "GB/s"
+GRID = (128, 96, 128)
+NCOMP = 3
+NSNAP = 1000
+CHUNK = 32
+K_RANK = 50
+L_SKETCH = 60
+STRIDE = (4, 4, 4)
+SEED = 0
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(grid=GRID, n=NSNAP):
+    m = NCOMP * grid[0] * grid[1] * grid[2]
+    return {"workload": f"streamed channel field {grid[0]}x{grid[1]}x{grid[2]}x{NCOMP} = "
+                        f"{m} rows x {n} snapshots FP32, chunks of {CHUNK}, l={L_SKETCH}, "
+                        f"k={K_RANK}, coarse {STRIDE[0]}x per direction",
+            "m": m, "n": n, "l": L_SKETCH, "k": K_RANK, "chunk": CHUNK,
+            "coarse_stride": list(STRIDE), "bytes_per_step": 4 * m * n,
+            "l2": "inputs larger than L2 (18.9 GB vs 129 MB); no flush needed",
+            "parallelism": "replicas (one independent matrix per GPU)"}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(kernel_file, kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1905_13257_gb300", "csrc", kernel_file), "rb").read()
+        ent = d.get(kernel_name)
+        if ent and ent.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            return float(ent["traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_uuid):
+        self.proc = None
+        self.uuid = dev_uuid
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_step(A_rows, grid_rows, ncomp_rows, n, k, l, seed):
+    """The oracle's hot path on a row sample: sketches, randomized ID, sub-sampled
+    ID of the sample's coarse rows, reconstruction error."""
+    import numpy as np
+    import oracle
+    A64 = np.asarray(A_rows, dtype=np.float64)
+    m = A64.shape[0]
+    Psi = oracle.psi(l, m, seed)
+    Om = oracle.omega(n, l, seed)
+    W, Y = oracle.sketch(A64, Psi, Om)
+    J, P, kout, _ = oracle.column_id(W, k)
+    rows = oracle.coarse_rows(grid_rows, ncomp_rows, STRIDE)
+    Jc, Pc, kc, _ = oracle.column_id(A64[rows], k)
+    fro, mx = oracle.recon_error(A64, J, P)
+    return fro
+
+
+def cpu_sample(A_host_rows, n, reps=1):
+    """Time the oracle on a row sample (the first y-planes of component u)."""
+    import numpy as np
+    nx, ny, nz = GRID
+    m_s = A_host_rows.shape[0]
+    ny_s = m_s // (nx * nz)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle_step(A_host_rows, (nx, ny_s, nz), 1, n, K_RANK, L_SKETCH, SEED)
+    dt = (time.perf_counter() - t0) / reps
+    return dt, f"rows 0..{m_s - 1} (component u, y-planes 0..{ny_s - 1}) x {n} snapshots"
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from synthetic.channel import factors
+    nx, ny, nz = GRID
+    ny_s = args.ref_planes
+    S, T = factors(GRID, NCOMP, NSNAP, SEED)
+    A_s = (S[: nx * nz * ny_s] @ T).to(torch.float32).numpy()
+    del S
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        cpu_sample(A_s, NSNAP)
+    times = []
+    for _ in range(args.steps):
+        dt, desc = cpu_sample(A_s, NSNAP)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    gbs = 4.0 * A_s.shape[0] * NSNAP / (ms / 1e3) / 1e9
+    cfg = workload()
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic channel field (seeded), FP32 values, oracle arithmetic FP64",
+            "config": cfg,
+            "cpu_baseline": {"value": gbs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": gbs, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1905_13257_gb300 import IdSketch, load
+    from synthetic import channel_field
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = load()
+
+    grid = GRID
+    cfgd = workload(grid, args.n)
+    m, n = cfgd["m"], cfgd["n"]
+    A = channel_field(grid, NCOMP, n, seed=SEED + rank, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sk = IdSketch(m, n, K_RANK, L_SKETCH, seed=SEED, dtype=torch.float32, grid=grid,
+                  ncomp=NCOMP, coarse_stride=STRIDE, want_Y=True, want_coarse=True,
+                  window_cols=n, stream=stream)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    phase_ms = {"sketch": 0.0, "factor": 0.0, "coarse": 0.0, "recon": 0.0}
+    result = {}
+
+    def step(record):
+        e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
+        e0.record(stream)
+        sk.reset()
+        for j0 in range(0, n, CHUNK):
+            sk.stream_columns(A[:, j0:j0 + CHUNK])
+        sk.flush()
+        e1.record(stream)
+        J, P, kout = sk.factor()
+        e2.record(stream)
+        Jc, Pc, kc = sk.coarse_factor()
+        e3.record(stream)
+        fro, mx = sk.reconstruct_error(A, J[:kout], P[:kout])
+        e4.record(stream)
+        if record:
+            e4.synchronize()
+            phase_ms["sketch"] += e0.elapsed_time(e1)
+            phase_ms["factor"] += e1.elapsed_time(e2)
+            phase_ms["coarse"] += e2.elapsed_time(e3)
+            phase_ms["recon"] += e3.elapsed_time(e4)
+        result.update(fro=fro, rel_max=mx, kout=kout, kc=kc)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    l0 = lib.id_kernel_launches()
+    t_start, t_end = ev(), ev()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.id_kernel_launches() - l0
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * 4.0 * m * n / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the fused sketch; one launch per step)
+    per_phase = {k: v / args.steps for k, v in phase_ms.items()}
+    peak, peak_kind = measured_peaks()
+    mc = NCOMP * math.ceil(grid[0] / STRIDE[0]) * math.ceil(grid[1] / STRIDE[1]) * \
+        math.ceil(grid[2] / STRIDE[2])
+    sketch_bytes = 4.0 * m * n + 4.0 * m * L_SKETCH + 4.0 * mc * n
+    launches_per_step = math.ceil(n / 320)
+    sketch_launch_ms = per_phase["sketch"] / launches_per_step
+    y_rmw = 8.0 * m * L_SKETCH * (launches_per_step - 1)
+    achieved = (sketch_bytes + y_rmw) / launches_per_step / (sketch_launch_ms / 1e3) / 1e9
+    roofline = {"kernel": "sketch_simt_kernel", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "peak_kind": f"of {peak_kind}", "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": kernel_traffic("sketch_simt.cu", "sketch_simt_kernel"),
+                "algorithmic_bytes_per_launch": (sketch_bytes + y_rmw) / launches_per_step,
+                "launch_ms": sketch_launch_ms, "phase_ms": per_phase}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A.T)
+        A_host_v = A_host.T
+        A_dev = torch.empty_like(A_host, device=dev).T
+
+        def e2e_step():
+            sk.reset()
+            for j0 in range(0, n, CHUNK):
+                A_dev[:, j0:j0 + CHUNK].copy_(A_host_v[:, j0:j0 + CHUNK], non_blocking=True)
+                sk.stream_columns(A_dev[:, j0:j0 + CHUNK])
+            J, P, kout = sk.factor(device="cpu")
+            Jc, Pc, kc = sk.coarse_factor(device="cpu")
+            fro, mx = sk.reconstruct_error(A_dev, J[:kout], P[:kout])
+            return J, P, Jc, Pc
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        for _ in range(args.steps):
+            J, P, Jc, Pc = e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s0.elapsed_time(s1) / args.steps
+        d2h = J.numel() * 4 + P.numel() * 8 + Jc.numel() * 4 + Pc.numel() * 8 + 16
+        e2e = {"value": world * 4.0 * m * n / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms}
+        del A_host, A_dev
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nx, ny, nz = grid
+        rows = nx * nz * args.cpu_planes
+        A_rows = A[:rows].T.contiguous().cpu().numpy().T
+        dt, desc = cpu_sample(A_rows, n)
+        cpu = {"value": 4.0 * rows * n / dt / 1e9, "unit": UNIT,
+               "cores": len(os.sched_getaffinity(0)), "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic channel field (seeded), resident in HBM",
+                "config": cfgd, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "cpu_baseline": cpu,
+                "errors": {"rel_fro": result.get("fro"), "rel_max": result.get("rel_max"),
+                           "k_out": result.get("kout"), "k_coarse": result.get("kc")}}
+        print(json.dumps(line), flush=True)
+    sk.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=NSNAP)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-planes", type=int, default=8,
+                    help="y-planes of component u in the CPU-baseline sample")
+    ap.add_argument("--ref-planes", type=int, default=2,
+                    help="y-planes per step of the reference arm's sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

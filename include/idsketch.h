@@ -1,0 +1,194 @@
+/*
+ * idsketch.h -- C ABI of the pass-efficient interpolative decomposition (ID)
+ * for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Dunton, Jofre, Iaccarino, Doostan, "Pass-efficient methods for
+ * compression of high-dimensional turbulent flow data" (arXiv:1905.13257).
+ *
+ * Orientation.  The paper's data matrix has one time snapshot per ROW and is
+ * compressed by a row ID  A ~ P A(I,:)  (Sec. 2.4, eq. eqn:id).  This library
+ * stores one snapshot per COLUMN: A is m x n with m = grid points x velocity
+ * components and n = snapshots, i.e. the paper's A transposed, and computes
+ * the column ID  A ~ A(:,J) P,  P (k x n), P(:,J) = I.  J is the paper's I and
+ * P is the paper's P transposed (Remark 2.1: row and column IDs are the same
+ * construction on A^T).
+ *
+ * Conventions for every call
+ *   - A and its column chunks are column-major: entry (i, j) at ptr[i + j*ld],
+ *     ld >= m, element type given by id_config.dtype.  They live in device
+ *     memory and stay owned by the caller.
+ *   - J holds 0-based column indices in pivot order (int32).
+ *   - P is row-major k x n FP64: entry (t, j) at P[t*n + j].
+ *   - Outputs J and P may be device or host pointers (copied with
+ *     cudaMemcpyDefault).  id_factor, id_coarse_factor and
+ *     id_reconstruct_error synchronise the stream before returning (they
+ *     read the pivot count or the error scalars on the host).
+ *   - All GPU work is enqueued on the CUDA stream given to id_sketch_create.
+ *   - Every call returns an id_status.  An argument error (ID_ERR_INVALID_ARG)
+ *     or a call out of order (ID_ERR_STATE) changes nothing.  After
+ *     ID_ERR_CUDA the handle is poisoned: every later call but
+ *     id_sketch_destroy returns ID_ERR_CUDA.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef IDSKETCH_H
+#define IDSKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ID_OK = 0,
+  ID_ERR_INVALID_ARG = 1,   /* bad pointer, size, stride or config field      */
+  ID_ERR_STATE = 2,         /* call out of order (e.g. factor before columns) */
+  ID_ERR_OOM = 3,           /* device allocation failed                      */
+  ID_ERR_CUDA = 4,          /* a CUDA runtime call or kernel failed          */
+  ID_ERR_RANK_DEFICIENT = 5,/* fewer than k pivots above the rank tolerance  */
+  ID_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                 */
+  ID_ERR_UNSUPPORTED = 7    /* valid request this build does not implement   */
+} id_status;
+
+typedef enum { ID_F32 = 0, ID_F64 = 1 } id_dtype;
+
+/* Arithmetic of the sketch products W = Psi A and Y = A Omega.
+ *   ID_SKETCH_EXACT: FP32-accurate (FP32 data) or FP64 (FP64 data) products.
+ *   ID_SKETCH_BF16:  A rounded to bfloat16 once, FP32 accumulation.
+ * The pivoted QR and the solve for P are FP64 in every mode. */
+typedef enum { ID_SKETCH_EXACT = 0, ID_SKETCH_BF16 = 1 } id_sketch_prec;
+
+/* Rank tolerance of the pivoted QR: pivoting stops when every residual
+ * column norm is <= ID_RANK_TOL_FACTOR * DBL_EPSILON * ||B||_F, B being the
+ * matrix factored (the paper's pseudo-inverse R11^+ of Algorithm 3 step 4 is
+ * then the inverse of the k_out x k_out non-singular R11). */
+#define ID_RANK_TOL_FACTOR 64.0
+
+typedef struct {
+  int64_t m;               /* rows of A = ncomp * nx * ny * nz (or any m > 0)  */
+  int64_t n_max;           /* column capacity: total columns streamed <= n_max */
+  int32_t k;               /* target rank, 1 <= k <= l                          */
+  int32_t l;               /* sketch width l = k + p, l <= 64                   */
+  uint64_t seed;           /* seed of Psi and Omega (Philox4x32-10 key)         */
+  int32_t dtype;           /* id_dtype of the streamed columns                  */
+  int32_t prec;            /* id_sketch_prec                                    */
+  int32_t grid[3];         /* nx, ny, nz; needed only for the coarse grid       */
+  int32_t ncomp;           /* velocity components; grid/ncomp unused if 0       */
+  int32_t coarse_stride[3];/* sx, sy, sz of the coarse grid (direct injection)  */
+  int32_t want_Y;          /* 1: also form Y = A Omega (m x l)                  */
+  int32_t want_coarse;     /* 1: gather A_c = A(rows_c, :) during the pass      */
+  int32_t window_cols;     /* columns aggregated per launch; 0 = process every
+                              id_sketch_stream_columns call at once (no borrow) */
+  int32_t reserved[4];     /* must be zero                                      */
+} id_config;
+
+typedef struct id_sketch id_sketch;   /* opaque, library-owned */
+
+/* Create a sketch state on the current device for one stream of snapshots.
+ * Draws Omega (n_max x l) from the counter generator, allocates W (l x n_max,
+ * FP64), Y (m x l, dtype) and A_c (m_c x n_max, dtype) as requested.
+ * Passage: Algorithm 4 steps 2-3 (Gaussian Omega, l = k + p; Sec. 2.2).
+ * cuda_stream may be NULL (legacy default stream).
+ * Errors: ID_ERR_INVALID_ARG for an inconsistent config (m <= 0, n_max <= 0,
+ * k < 1, k > l, l > 64, grid/ncomp not matching m when want_coarse, a coarse
+ * stride < 1, reserved fields != 0), ID_ERR_OOM, ID_ERR_CUDA. */
+id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** out);
+
+/* Stream ncols snapshot columns (device pointer, column-major, leading
+ * dimension ld >= m) into the sketch: W(:, cols) = Psi A(:, cols) and
+ * Y += A(:, cols) Omega(cols, :) in ONE read of the columns; the coarse rows
+ * A_c(:, cols) are gathered in the same read when want_coarse.
+ * Passage: Sec. 2.1 (snapshots arrive one at a time, the count is not known
+ * in advance) and Algorithm 4 step 3 / eq. eq:sampmatrix.
+ * Ownership: with window_cols == 0 the columns are read before the call
+ * returns (in stream order).  With window_cols > 0 the chunk is BORROWED until
+ * the window is launched (window full, id_sketch_flush, id_factor,
+ * id_coarse_factor, id_sketch_get or id_sketch_destroy): the caller must not
+ * overwrite it before then.  Consecutive chunks of one buffer are merged into
+ * one launch.  Streaming may continue after id_factor (the sketches are
+ * linear in the columns); a later id_factor covers every column so far.
+ * Errors: ID_ERR_INVALID_ARG (null pointer, ld < m, ncols < 0, total columns
+ * > n_max). */
+id_status id_sketch_stream_columns(id_sketch* h, const void* d_cols, int64_t ld, int64_t ncols);
+
+/* Launch every pending (borrowed) chunk now.  Afterwards no chunk is borrowed. */
+id_status id_sketch_flush(id_sketch* h);
+
+/* Start a new stream of snapshots with the same config and buffers
+ * (columns seen -> 0, W and Y cleared).  Pending chunks are dropped. */
+id_status id_sketch_reset(id_sketch* h);
+
+/* Randomized ID of the streamed columns from the small sketch W = Psi A:
+ * k-step column-pivoted Householder QR of W (FP64) -> skeleton J, then
+ * C = R11^{-1} R12 by back-substitution and P(:,J) = I, P(:,Jc) = C.
+ * Passage: Algorithm 4 steps 4-8 (transposed orientation), Sec. 2.4.
+ * J: k ints; P: k x n_seen FP64 row-major (host or device).  k_out (host, may
+ * be NULL) receives the pivots taken.  n = columns streamed so far.
+ * Pivot rule: largest residual column norm, recomputed at every step; ties go
+ * to the lowest column index.
+ * Returns ID_ERR_RANK_DEFICIENT when fewer than k pivots clear the rank
+ * tolerance; J and the first k_out rows of P are still valid.
+ * Errors: ID_ERR_STATE when no column was streamed. */
+id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out);
+
+/* Sub-sampled ID (Algorithm 5, transposed): deterministic k-step
+ * column-pivoted QR (FP64) of the coarse matrix A_c = A(rows_c, :) gathered
+ * during the pass, then P_c as in id_factor.  The pair induces the lifted ID
+ * A ~ A(:, J_c) P_c of eq. eq:coarseregA.  rows_c = every stride-th grid index
+ * in x, y, z from 0, all components, row r = ((c*ny + j)*nz + kz)*nx + i.
+ * Errors: ID_ERR_STATE without want_coarse or without columns. */
+id_status id_coarse_factor(id_sketch* h, int32_t* Jc, double* Pc, int32_t* k_out);
+
+/* Errors of the reconstruction A_hat = A(:,J) P over an m x n matrix in ONE
+ * read of A (device, column-major, lda >= m, the handle's dtype):
+ *   rel_fro = ||A - A_hat||_F / ||A||_F                (Sec. 3.3 metric)
+ *   rel_max = max_ij |A_ij - A_hat_ij| / |A_ij| over A_ij != 0 (Sec. 3.1)
+ * J (k ints) and P (k x n FP64 row-major) may be host or device pointers;
+ * rel_fro / rel_max are host pointers (the call synchronises the stream);
+ * either may be NULL.  k may be smaller than the handle's k (e.g. k_out).
+ * Errors: ID_ERR_INVALID_ARG (null A, lda < m, n < 1, k < 1, k > 64,
+ * J entry outside [0, n)). */
+id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64_t n,
+                               const int32_t* J, const double* P, int32_t k,
+                               double* rel_fro, double* rel_max);
+
+/* Borrow the device buffers of the sketch (valid until reset/destroy):
+ *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])
+ *   Y  m x l, dtype, column-major (entry (i, s) at Y[i + s*m]); NULL unless want_Y
+ *   Ac m_c x n_max, dtype, column-major; NULL unless want_coarse
+ * Any output pointer may be NULL.  Pending chunks are flushed first. */
+id_status id_sketch_get(id_sketch* h, const double** d_W, const void** d_Y, const void** d_Ac,
+                        int64_t* n_seen, int64_t* m_c);
+
+/* Release every device buffer of the handle (synchronises its stream). */
+void id_sketch_destroy(id_sketch* h);
+
+/* Fill out[(i - first) * width + s] = G(i, s) for i in [first, first+count),
+ * s in [0, width): the same counter-based Gaussian entries the sketch uses,
+ * which = 1 for Psi (G(i,s) = Psi[s, i]) and which = 2 for Omega
+ * (G(j,s) = Omega[j, s]).  Definition (the paper only asks for i.i.d.
+ * Gaussian entries, Sec. 2.2): Philox4x32-10 with key (seed lo, seed hi),
+ * counter (i lo, i hi, s / 10, which); field s % 10 (12 bits) of the 128-bit
+ * output indexes the 4096 mid-point normal quantiles rounded to bfloat16.
+ * d_out: device FP32 buffer of count*width entries; enqueued on cuda_stream. */
+id_status id_gaussian_fill(int32_t which, uint64_t seed, int64_t first, int64_t count,
+                           int32_t width, float* d_out, void* cuda_stream);
+
+/* Host-only: the 4096-entry quantile table as bfloat16 bit patterns. */
+id_status id_gaussian_table(uint16_t out[4096]);
+
+/* Number of kernels this library has launched in the process so far (all
+ * handles, all devices); for accounting in benchmarks. */
+int64_t id_kernel_launches(void);
+
+/* Static string for a status code. */
+const char* id_status_str(id_status s);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t id_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDSKETCH_H */

@@ -1,0 +1,173 @@
+"""Python front end of the C ABI, with PyTorch tensors for device memory and
+streams.  Argument marshalling only: every step runs in libidsketch.so.
+
+Layout conventions (as in include/idsketch.h): a snapshot matrix is an m x n
+column-major torch view (strides (1, ld)), e.g. ``At.T`` for a contiguous
+(n, m) tensor; J is int32 in pivot order; P is a row-major (k, n) FP64 tensor.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _binding as B
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream), stream
+
+
+def _colmajor(A, m):
+    if A.dim() != 2 or A.shape[0] != m:
+        raise ValueError(f"expected an ({m}, n) column-major tensor, got {tuple(A.shape)}")
+    if A.shape[1] > 1 and A.stride(0) != 1:
+        raise ValueError("columns must be contiguous (stride(0) == 1)")
+    ld = A.stride(1) if A.shape[1] > 1 else max(A.stride(1), m)
+    return ld
+
+
+class _DeviceView:
+    """Zero-copy torch view of library-owned device memory."""
+
+    def __init__(self, ptr, shape, strides_bytes, typestr):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "strides": tuple(strides_bytes), "typestr": typestr,
+            "data": (int(ptr), False), "version": 2,
+        }
+
+
+class IdSketch:
+    """One stream of snapshot columns compressed by the pass-efficient ID."""
+
+    def __init__(self, m, n_max, k, l, seed=0, dtype=torch.float32, prec="exact",
+                 grid=None, ncomp=0, coarse_stride=None, want_Y=True, want_coarse=False,
+                 window_cols=0, stream=None):
+        self.lib = B.load()
+        cfg = B.IdConfig()
+        cfg.m, cfg.n_max, cfg.k, cfg.l, cfg.seed = m, n_max, k, l, seed
+        cfg.dtype = B.ID_F64 if dtype == torch.float64 else B.ID_F32
+        cfg.prec = B.ID_SKETCH_BF16 if prec == "bf16" else B.ID_SKETCH_EXACT
+        if grid is not None:
+            cfg.grid[:] = list(grid)
+        cfg.ncomp = ncomp
+        if coarse_stride is not None:
+            cfg.coarse_stride[:] = list(coarse_stride)
+        cfg.want_Y = int(bool(want_Y))
+        cfg.want_coarse = int(bool(want_coarse))
+        cfg.window_cols = int(window_cols)
+        self.cfg = cfg
+        self.m, self.n_max, self.k, self.l = m, n_max, k, l
+        self.dtype = dtype
+        self._sh, self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        B.check(self.lib.id_sketch_create(C.byref(cfg), self._sh, C.byref(h)), "id_sketch_create")
+        self.h = h
+        self._keep = []   # borrowed chunks stay referenced until launched
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.id_sketch_destroy(self.h)
+            self.h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stream_columns(self, cols):
+        ld = _colmajor(cols, self.m)
+        if cols.dtype != self.dtype or not cols.is_cuda:
+            raise ValueError("columns must be CUDA tensors of the sketch dtype")
+        B.check(self.lib.id_sketch_stream_columns(self.h, C.c_void_p(cols.data_ptr()), ld,
+                                                  cols.shape[1]), "id_sketch_stream_columns")
+        if self.cfg.window_cols:
+            self._keep.append(cols)
+
+    def flush(self):
+        B.check(self.lib.id_sketch_flush(self.h), "id_sketch_flush")
+        self._keep = []
+
+    def reset(self):
+        B.check(self.lib.id_sketch_reset(self.h), "id_sketch_reset")
+        self._keep = []
+
+    def n_seen(self):
+        n = C.c_int64()
+        B.check(self.lib.id_sketch_get(self.h, None, None, None, C.byref(n), None), "id_sketch_get")
+        return n.value
+
+    def _factor(self, fn, name, device):
+        n = self.n_seen()
+        dev = self.stream.device if device == "cuda" else torch.device("cpu")
+        J = torch.empty(self.k, dtype=torch.int32, device=dev)
+        P = torch.empty((self.k, n), dtype=torch.float64, device=dev)
+        kout = C.c_int32()
+        st = fn(self.h, C.c_void_p(J.data_ptr()), C.c_void_p(P.data_ptr()), C.byref(kout))
+        B.check(st, name, allow=(B.ID_ERR_RANK_DEFICIENT,))
+        self._keep = []
+        return J, P, kout.value
+
+    def factor(self, device="cuda"):
+        """Randomized ID from W = Psi A: returns (J, P, k_out)."""
+        return self._factor(self.lib.id_factor, "id_factor", device)
+
+    def coarse_factor(self, device="cuda"):
+        """Sub-sampled ID from the coarse rows: returns (J_c, P_c, k_out)."""
+        return self._factor(self.lib.id_coarse_factor, "id_coarse_factor", device)
+
+    def reconstruct_error(self, A, J, P, k=None):
+        ld = _colmajor(A, self.m)
+        k = int(J.numel()) if k is None else int(k)
+        J = J.to(torch.int32).contiguous()
+        P = P.to(torch.float64).contiguous()
+        fro, mx = C.c_double(), C.c_double()
+        B.check(self.lib.id_reconstruct_error(self.h, C.c_void_p(A.data_ptr()), ld, A.shape[1],
+                                              C.c_void_p(J.data_ptr()), C.c_void_p(P.data_ptr()),
+                                              k, C.byref(fro), C.byref(mx)),
+                "id_reconstruct_error")
+        return fro.value, mx.value
+
+    def sketches(self):
+        """Zero-copy views (W (l, n) FP64, Y (m, l) or None, A_c (m_c, n) or None)."""
+        w, y, ac = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        n, mc = C.c_int64(), C.c_int64()
+        B.check(self.lib.id_sketch_get(self.h, C.byref(w), C.byref(y), C.byref(ac), C.byref(n),
+                                       C.byref(mc)), "id_sketch_get")
+        n = n.value
+        es = 8 if self.dtype == torch.float64 else 4
+        ts = "<f8" if self.dtype == torch.float64 else "<f4"
+        dev = self.stream.device
+        W = torch.as_tensor(_DeviceView(w.value, (self.l, n), (8 * self.n_max, 8), "<f8"),
+                            device=dev)
+        Y = None
+        if y.value:
+            Y = torch.as_tensor(_DeviceView(y.value, (self.m, self.l), (es, es * self.m), ts),
+                                device=dev)
+        Ac = None
+        if ac.value and n > 0:
+            Ac = torch.as_tensor(_DeviceView(ac.value, (mc.value, n), (es, es * mc.value), ts),
+                                 device=dev)
+        return W, Y, Ac
+
+
+def gaussian_fill(which, seed, first, count, width, device=None, stream=None):
+    """The counter-based Gaussian entries (which=1 Psi, 2 Omega) as a (count, width)
+    FP32 CUDA tensor: row i holds G(first + i, 0:width)."""
+    lib = B.load()
+    sh, stream = _stream_handle(stream)
+    out = torch.empty((count, width), dtype=torch.float32, device=stream.device)
+    B.check(lib.id_gaussian_fill(which, seed, first, count, width, C.c_void_p(out.data_ptr()), sh),
+            "id_gaussian_fill")
+    return out
+
+
+def gaussian_table_bits():
+    lib = B.load()
+    buf = (C.c_uint16 * 4096)()
+    B.check(lib.id_gaussian_table(buf), "id_gaussian_table")
+    return [int(x) for x in buf]

@@ -1,0 +1,462 @@
+// C ABI of the pass-efficient ID (declared in include/idsketch.h): handle
+// lifecycle, column windows, argument checks and host/device outputs.  Every
+// arithmetic step runs in the kernels of this directory.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <new>
+
+#include "idsk_internal.h"
+
+using namespace idsk;
+
+namespace idsk {
+int coarse_blocks_needed(int64_t mc, int nsm);
+
+std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_table_mu;
+float* g_table[kMaxDevices] = {nullptr};
+
+// Device copy of the quantile table, one per device for the process lifetime.
+cudaError_t device_table(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  if (!g_table[dev]) {
+    float host[kTableSize];
+    gaussian_table_host(host, nullptr);
+    float* d = nullptr;
+    e = cudaMalloc(&d, sizeof(host));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, host, sizeof(host), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return e;
+    }
+    g_table[dev] = d;
+  }
+  *out = g_table[dev];
+  return cudaSuccess;
+}
+
+// Optional allocation cap (bytes) for fault-injection tests.
+size_t alloc_cap() {
+  const char* s = getenv("IDSKETCH_ALLOC_CAP_BYTES");
+  if (!s || !*s) return (size_t)-1;
+  return (size_t)strtoull(s, nullptr, 10);
+}
+
+struct Allocator {
+  size_t used = 0, cap = alloc_cap();
+  id_status st = ID_OK;
+  template <class T>
+  void get(T** p, size_t count) {
+    if (st != ID_OK || count == 0) return;
+    const size_t bytes = count * sizeof(T);
+    if (used + bytes > cap) {
+      st = ID_ERR_OOM;
+      return;
+    }
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      st = ID_ERR_OOM;
+      return;
+    }
+    if (e != cudaSuccess) {
+      st = ID_ERR_CUDA;
+      return;
+    }
+    used += bytes;
+  }
+};
+
+void free_all(id_sketch* h) {
+  void* ptrs[] = {h->d_omega, h->d_W, h->d_Y, h->d_Ac, h->d_work, h->d_R, h->d_P, h->d_J,
+                  h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gpart,
+                  h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
+                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+id_status validate(const id_config* c) {
+  if (!c) return ID_ERR_INVALID_ARG;
+  if (c->m <= 0 || c->n_max <= 0 || c->n_max > (int64_t)1 << 30) return ID_ERR_INVALID_ARG;
+  if (c->k < 1 || c->l < c->k || c->l > kLMax) return ID_ERR_INVALID_ARG;
+  if (c->dtype != ID_F32 && c->dtype != ID_F64) return ID_ERR_INVALID_ARG;
+  if (c->prec != ID_SKETCH_EXACT && c->prec != ID_SKETCH_BF16) return ID_ERR_INVALID_ARG;
+  if (c->prec == ID_SKETCH_BF16 && c->dtype != ID_F32) return ID_ERR_INVALID_ARG;
+  if (c->window_cols < 0) return ID_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (c->reserved[i] != 0) return ID_ERR_INVALID_ARG;
+  if (c->want_coarse) {
+    if (c->ncomp < 1) return ID_ERR_INVALID_ARG;
+    int64_t pts = c->ncomp;
+    for (int d = 0; d < 3; ++d) {
+      if (c->grid[d] < 1 || c->coarse_stride[d] < 1) return ID_ERR_INVALID_ARG;
+      pts *= c->grid[d];
+    }
+    if (pts != c->m) return ID_ERR_INVALID_ARG;
+  }
+  if (c->n_max > 32 * 1024) return ID_ERR_INVALID_ARG;   // one-CTA pivoted QR limit
+  return ID_OK;
+}
+
+#define IDSK_CUDA(h, expr)                \
+  do {                                    \
+    cudaError_t e_ = (expr);              \
+    if (e_ != cudaSuccess) {              \
+      (h)->poisoned = true;               \
+      return ID_ERR_CUDA;                 \
+    }                                     \
+  } while (0)
+
+id_status launch_pending(id_sketch* h) {
+  while (!h->pend.empty()) {
+    Window w;
+    memset(&w, 0, sizeof(w));
+    w.col_base = h->n_launched;
+    const int wmax = kSimtWindowMax;
+    int taken = 0;
+    size_t consumed = 0;
+    while (consumed < h->pend.size() && w.nseg < kMaxSegs && taken < wmax) {
+      Seg& s = h->pend[consumed];
+      const int use = std::min(s.ncols, wmax - taken);
+      Seg part = s;
+      part.col0 = taken;
+      part.ncols = use;
+      w.seg[w.nseg++] = part;
+      taken += use;
+      if (use == s.ncols) {
+        ++consumed;
+      } else {
+        s.ptr = (const char*)s.ptr + (size_t)use * s.ld * h->esz;
+        s.ncols -= use;
+      }
+    }
+    h->pend.erase(h->pend.begin(), h->pend.begin() + consumed);
+    w.ncols = taken;
+
+    SketchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = h->m;
+    a.l = h->l;
+    a.lpad = h->lpad;
+    a.k0 = h->key0;
+    a.k1 = h->key1;
+    a.table = h->d_table;
+    a.omega = h->d_omega;
+    a.W = h->d_W;
+    a.ldw = h->n_max;
+    a.Y = h->d_Y;
+    a.want_Y = h->cfg.want_Y ? 1 : 0;
+    a.y_accumulate = h->y_started ? 1 : 0;
+    a.Ac = h->d_Ac;
+    a.cg = h->cg;
+    a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
+    IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, h->nsm, h->st));
+    h->y_started = true;
+    h->n_launched += taken;
+  }
+  h->pend_cols = 0;
+  return ID_OK;
+}
+
+id_status copy_out(id_sketch* h, void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return ID_OK;
+  IDSK_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->st));
+  return ID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* id_status_str(id_status s) {
+  switch (s) {
+    case ID_OK: return "ok";
+    case ID_ERR_INVALID_ARG: return "invalid argument";
+    case ID_ERR_STATE: return "call out of order";
+    case ID_ERR_OOM: return "out of device memory";
+    case ID_ERR_CUDA: return "CUDA error";
+    case ID_ERR_RANK_DEFICIENT: return "rank deficient: fewer than k pivots";
+    case ID_ERR_TIMEOUT: return "device wait timed out";
+    case ID_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+int32_t id_version(void) { return 100; }
+
+int64_t id_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+id_status id_gaussian_table(uint16_t out[4096]) {
+  if (!out) return ID_ERR_INVALID_ARG;
+  gaussian_table_host(nullptr, out);
+  return ID_OK;
+}
+
+id_status id_gaussian_fill(int32_t which, uint64_t seed, int64_t first, int64_t count,
+                           int32_t width, float* d_out, void* cuda_stream) {
+  if ((which != (int32_t)kStreamPsi && which != (int32_t)kStreamOmega) || first < 0 ||
+      count < 0 || width < 1 || (count > 0 && !d_out))
+    return ID_ERR_INVALID_ARG;
+  if (count == 0) return ID_OK;
+  float* tab = nullptr;
+  if (device_table(&tab) != cudaSuccess) return ID_ERR_CUDA;
+  cudaError_t e = launch_gaussian_fill((uint32_t)which, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                       first, count, width, tab, d_out,
+                                       (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? ID_OK : ID_ERR_CUDA;
+}
+
+id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** out) {
+  if (!out) return ID_ERR_INVALID_ARG;
+  *out = nullptr;
+  id_status v = validate(cfg);
+  if (v != ID_OK) return v;
+  id_sketch* h = new (std::nothrow) id_sketch();
+  if (!h) return ID_ERR_OOM;
+  h->cfg = *cfg;
+  h->st = (cudaStream_t)cuda_stream;
+  h->m = cfg->m;
+  h->n_max = cfg->n_max;
+  h->k = cfg->k;
+  h->l = cfg->l;
+  h->lpad = ((cfg->l + 15) / 16) * 16;
+  h->esz = cfg->dtype == ID_F64 ? 8 : 4;
+  h->key0 = (uint32_t)cfg->seed;
+  h->key1 = (uint32_t)(cfg->seed >> 32);
+  if (cudaGetDevice(&h->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return ID_ERR_CUDA;
+  }
+  if (cfg->want_coarse) {
+    CoarseGeom& g = h->cg;
+    g.on = 1;
+    g.nx = cfg->grid[0];
+    g.ny = cfg->grid[1];
+    g.nz = cfg->grid[2];
+    g.sx = cfg->coarse_stride[0];
+    g.sy = cfg->coarse_stride[1];
+    g.sz = cfg->coarse_stride[2];
+    g.cx = (g.nx + g.sx - 1) / g.sx;
+    g.cy = (g.ny + g.sy - 1) / g.sy;
+    g.cz = (g.nz + g.sz - 1) / g.sz;
+    g.mc = (int64_t)cfg->ncomp * g.cx * g.cy * g.cz;
+    h->mc = g.mc;
+  }
+  if (device_table(&h->d_table) != cudaSuccess) {
+    delete h;
+    return ID_ERR_CUDA;
+  }
+  const int64_t nm = h->n_max;
+  const int k = h->k, l = h->l;
+  Allocator al;
+  al.get(&h->d_omega, (size_t)nm * l);
+  al.get(&h->d_W, (size_t)l * nm);
+  if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);
+  if (cfg->want_coarse) al.get((char**)&h->d_Ac, (size_t)h->mc * nm * h->esz);
+  al.get(&h->d_work, (size_t)l * nm);
+  al.get(&h->d_R, (size_t)k * nm);
+  al.get(&h->d_P, (size_t)k * nm);
+  al.get(&h->d_J, (size_t)k);
+  al.get(&h->d_colpos, (size_t)nm);
+  al.get(&h->d_kout, 1);
+  h->rec_blocks = 8 * h->nsm;
+  al.get(&h->d_part, (size_t)3 * h->rec_blocks);
+  al.get(&h->d_out3, 3);
+  al.get(&h->d_Jin, (size_t)kRecKMax);
+  if (cfg->want_coarse) {
+    h->coarse_blocks = coarse_blocks_needed(h->mc, h->nsm);
+    al.get(&h->d_V, (size_t)h->mc * k);
+    al.get(&h->d_F, (size_t)nm * k);
+    al.get(&h->d_nu2, (size_t)nm);
+    al.get(&h->d_nu20, (size_t)nm);
+    al.get(&h->d_gpart, (size_t)h->coarse_blocks * (nm + kLMax));
+    al.get(&h->d_upart, (size_t)h->coarse_blocks);
+    al.get(&h->d_cscal, 8);
+    al.get(&h->d_cint, 4);
+    al.get(&h->d_rlist, (size_t)nm);
+    al.get(&h->d_Rc, (size_t)k * nm);
+    al.get(&h->d_Pc, (size_t)k * nm);
+    al.get(&h->d_Jc, (size_t)k);
+    al.get(&h->d_colposc, (size_t)nm);
+  }
+  if (al.st != ID_OK) {
+    free_all(h);
+    delete h;
+    return al.st;
+  }
+  cudaError_t e = launch_gaussian_fill(kStreamOmega, h->key0, h->key1, 0, nm, l, h->d_table,
+                                       h->d_omega, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_W, 0, sizeof(double) * l * nm, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return ID_ERR_CUDA;
+  }
+  *out = h;
+  return ID_OK;
+}
+
+id_status id_sketch_stream_columns(id_sketch* h, const void* d_cols, int64_t ld, int64_t ncols) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (ncols < 0 || (ncols > 0 && (!d_cols || ld < h->m))) return ID_ERR_INVALID_ARG;
+  if (h->n_seen + ncols > h->n_max) return ID_ERR_INVALID_ARG;
+  if (ncols == 0) return ID_OK;
+  Seg s;
+  s.ptr = d_cols;
+  s.ld = ld;
+  s.col0 = 0;
+  s.ncols = (int32_t)ncols;
+  if (!h->pend.empty()) {
+    Seg& b = h->pend.back();
+    const char* end = (const char*)b.ptr + (size_t)b.ncols * b.ld * h->esz;
+    if (b.ld == ld && end == (const char*)d_cols) {
+      b.ncols += (int32_t)ncols;
+    } else {
+      h->pend.push_back(s);
+    }
+  } else {
+    h->pend.push_back(s);
+  }
+  h->n_seen += ncols;
+  h->pend_cols += ncols;
+  if (h->cfg.window_cols == 0 || h->pend_cols >= h->cfg.window_cols) return launch_pending(h);
+  return ID_OK;
+}
+
+id_status id_sketch_flush(id_sketch* h) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  return launch_pending(h);
+}
+
+id_status id_sketch_reset(id_sketch* h) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  h->pend.clear();
+  h->pend_cols = 0;
+  h->n_seen = 0;
+  h->n_launched = 0;
+  h->y_started = false;
+  IDSK_CUDA(h, cudaMemsetAsync(h->d_W, 0, sizeof(double) * h->l * h->n_max, h->st));
+  return ID_OK;
+}
+
+id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  const int64_t n = h->n_seen;
+  if (n == 0) return ID_ERR_STATE;
+  const int k = h->k, l = h->l;
+  IDSK_CUDA(h, cudaMemcpy2DAsync(h->d_work, sizeof(double) * n, h->d_W,
+                                 sizeof(double) * h->n_max, sizeof(double) * n, l,
+                                 cudaMemcpyDeviceToDevice, h->st));
+  IDSK_CUDA(h, launch_cpqr_small(h->d_work, l, (int)n, (int)n, k, ID_RANK_TOL_FACTOR, h->d_R,
+                                 h->d_J, h->d_colpos, h->d_kout, h->st));
+  IDSK_CUDA(h, launch_solve_p(h->d_R, h->d_J, h->d_colpos, h->d_kout, k, (int)n, h->d_P, h->st));
+  if ((s = copy_out(h, J, h->d_J, sizeof(int32_t) * k)) != ID_OK) return s;
+  if ((s = copy_out(h, P, h->d_P, sizeof(double) * k * n)) != ID_OK) return s;
+  int32_t kk = 0;
+  IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_kout, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (k_out) *k_out = kk;
+  return kk < k ? ID_ERR_RANK_DEFICIENT : ID_OK;
+}
+
+id_status id_coarse_factor(id_sketch* h, int32_t* Jc, double* Pc, int32_t* k_out) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!h->cfg.want_coarse) return ID_ERR_STATE;
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  const int64_t n = h->n_seen;
+  if (n == 0) return ID_ERR_STATE;
+  const int k = h->k;
+  IDSK_CUDA(h, launch_coarse_cpqr(h, n, h->st));
+  if ((s = copy_out(h, Jc, h->d_Jc, sizeof(int32_t) * k)) != ID_OK) return s;
+  if ((s = copy_out(h, Pc, h->d_Pc, sizeof(double) * k * n)) != ID_OK) return s;
+  int32_t kk = 0;
+  IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_cint + 3, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (k_out) *k_out = kk;
+  return kk < k ? ID_ERR_RANK_DEFICIENT : ID_OK;
+}
+
+id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64_t n,
+                               const int32_t* J, const double* P, int32_t k, double* rel_fro,
+                               double* rel_max) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!d_A || !J || !P || lda < h->m || n < 1 || k < 1 || k > kRecKMax)
+    return ID_ERR_INVALID_ARG;
+  int32_t jh[kRecKMax];
+  IDSK_CUDA(h, cudaMemcpyAsync(jh, J, sizeof(int32_t) * k, cudaMemcpyDefault, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  for (int u = 0; u < k; ++u)
+    if (jh[u] < 0 || jh[u] >= n) return ID_ERR_INVALID_ARG;
+  if ((int64_t)k * n > h->pin_cap) {
+    if (h->d_Pin) cudaFree(h->d_Pin);
+    h->d_Pin = nullptr;
+    h->pin_cap = 0;
+    Allocator al;
+    al.get(&h->d_Pin, (size_t)k * n);
+    if (al.st != ID_OK) return al.st;
+    h->pin_cap = (int64_t)k * n;
+  }
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_Jin, jh, sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_Pin, P, sizeof(double) * k * n, cudaMemcpyDefault, h->st));
+  IDSK_CUDA(h, launch_recon_error(d_A, lda, h->m, n, h->cfg.dtype, h->d_Jin, h->d_Pin, k,
+                                  h->d_part, h->rec_blocks, h->d_out3, h->st));
+  double o[3];
+  IDSK_CUDA(h, cudaMemcpyAsync(o, h->d_out3, sizeof(o), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (rel_fro) *rel_fro = o[1] > 0.0 ? sqrt(o[0] / o[1]) : 0.0;
+  if (rel_max) *rel_max = o[2];
+  return ID_OK;
+}
+
+id_status id_sketch_get(id_sketch* h, const double** d_W, const void** d_Y, const void** d_Ac,
+                        int64_t* n_seen, int64_t* m_c) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  if (d_W) *d_W = h->d_W;
+  if (d_Y) *d_Y = h->d_Y;
+  if (d_Ac) *d_Ac = h->d_Ac;
+  if (n_seen) *n_seen = h->n_seen;
+  if (m_c) *m_c = h->mc;
+  return ID_OK;
+}
+
+void id_sketch_destroy(id_sketch* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Column-pivoted Householder QR of the small sketch W (l x n, FP64) and the
+// solve for the interpolation matrix P.
+//
+// Algorithm 4 steps 4-8 (transposed): k pivots of a column-pivoted QR of W
+// select the skeleton J; C = R11^{-1} R12 by back-substitution; P(:,J) = I,
+// P(:,Jc) = C.  The paper's QR is pivoted modified Gram-Schmidt (mgsqr,
+// Sec. 2.4); Householder reflections with the same pivot rule give the same
+// pivots and R in exact arithmetic and are the stabler choice.
+//
+// Pivot rule: the largest residual column norm ||W^(s)(s:, j)||, recomputed
+// from the updated matrix at every step (no downdating), ties to the lowest
+// column index.  One CTA of 1024 threads works in place on a copy of W held
+// row-major in global memory (L2-resident: l x n x 8 bytes); thread t owns
+// columns t, t + 1024, ...  Norms and the argmax use warp shuffles; the
+// reflector of the pivot column is formed by one warp.
+#include <float.h>
+
+#include "idsk_internal.h"
+
+namespace idsk {
+namespace {
+
+constexpr int NT = 1024;
+constexpr int QMAX = 32;   // columns per thread -> n <= 32768
+
+struct ArgMax {
+  double v;
+  int i;
+};
+
+__device__ __forceinline__ ArgMax better(ArgMax a, ArgMax b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax b;
+    b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+    b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+    a = better(a, b);
+  }
+  return a;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(NT, 1)
+cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double tol_factor,
+                  double* __restrict__ R, int* __restrict__ J, int* __restrict__ colpos,
+                  int* __restrict__ kout) {
+  __shared__ ArgMax red[NT / 32];
+  __shared__ double vs[kLMax];
+  __shared__ double sh_tau, sh_beta, sh_tol;
+  __shared__ int sh_p, sh_stop;
+  __shared__ double fro_part[NT / 32];
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int kmax = min(k, min(rows, n));
+  uint32_t pivoted = 0u;   // bit q: column t + q*NT was pivoted
+
+  // ||M||_F for the rank tolerance
+  {
+    double ss = 0.0;
+    for (int q = 0; q < QMAX; ++q) {
+      const int j = t + q * NT;
+      if (j >= n) break;
+      for (int i = 0; i < rows; ++i) {
+        const double x = M[(int64_t)i * ld + j];
+        ss += x * x;
+      }
+      colpos[j] = -1;
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) fro_part[warp] = ss;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += fro_part[w];
+      sh_tol = tol_factor * DBL_EPSILON * sqrt(s);
+    }
+    __syncthreads();
+  }
+
+  int s = 0;
+  for (; s < kmax; ++s) {
+    // residual norms of the non-pivoted columns
+    ArgMax best{-1.0, 0x7fffffff};
+    for (int q = 0; q < QMAX; ++q) {
+      const int j = t + q * NT;
+      if (j >= n) break;
+      if (pivoted & (1u << q)) continue;
+      double ss = 0.0;
+      for (int i = s; i < rows; ++i) {
+        const double x = M[(int64_t)i * ld + j];
+        ss += x * x;
+      }
+      best = better(best, ArgMax{sqrt(ss), j});
+    }
+    best = warp_argmax(best);
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+      ArgMax b = red[lane];
+      b = warp_argmax(b);
+      if (lane == 0) {
+        sh_p = b.i;
+        sh_stop = !(b.v > sh_tol);
+      }
+    }
+    __syncthreads();
+    if (sh_stop) break;
+    const int p = sh_p;
+    // Householder reflector of the pivot column, rows s..rows-1 (one warp)
+    if (warp == 0) {
+      const int len = rows - s;
+      double x0 = (lane < len) ? M[(int64_t)(s + lane) * ld + p] : 0.0;
+      double x1 = (lane + 32 < len) ? M[(int64_t)(s + lane + 32) * ld + p] : 0.0;
+      const double alpha = __shfl_sync(0xffffffffu, x0, 0);
+      const double sigma = warp_sum((lane == 0 ? 0.0 : x0 * x0) + x1 * x1);
+      double tau = 0.0, beta = alpha, scale = 0.0;
+      if (sigma != 0.0) {
+        const double nrm = sqrt(alpha * alpha + sigma);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = alpha - beta;
+      }
+      if (lane < len) vs[lane] = lane == 0 ? 1.0 : (sigma != 0.0 ? x0 / scale : 0.0);
+      if (lane + 32 < len) vs[lane + 32] = sigma != 0.0 ? x1 / scale : 0.0;
+      if (lane == 0) {
+        sh_tau = tau;
+        sh_beta = beta;
+        J[s] = p;
+        colpos[p] = s;
+      }
+    }
+    __syncthreads();
+    const double tau = sh_tau;
+    // apply H = I - tau v v^T to the other non-pivoted columns; emit row s of R
+    for (int q = 0; q < QMAX; ++q) {
+      const int j = t + q * NT;
+      if (j >= n) break;
+      double rsj;
+      if (j == p) {
+        pivoted |= (1u << q);
+        rsj = sh_beta;
+      } else if (pivoted & (1u << q)) {
+        rsj = 0.0;
+      } else {
+        if (tau != 0.0) {
+          double d = 0.0;
+          for (int i = s; i < rows; ++i) d += vs[i - s] * M[(int64_t)i * ld + j];
+          const double td = tau * d;
+          for (int i = s; i < rows; ++i) M[(int64_t)i * ld + j] -= td * vs[i - s];
+        }
+        rsj = M[(int64_t)s * ld + j];
+      }
+      R[(int64_t)s * n + j] = rsj;
+    }
+    __syncthreads();
+  }
+  if (t == 0) *kout = s;
+  for (int q = s + t; q < k; q += NT) J[q] = -1;
+}
+
+// P(:, j) for every column j: e_u when j = J[u]; otherwise the solution of
+// R11 x = R(:, j) by back-substitution, R11(t, u) = R(t, J[u]).
+__global__ void solve_p_kernel(const double* __restrict__ R, const int* __restrict__ J,
+                               const int* __restrict__ colpos, const int* __restrict__ kout,
+                               int k, int n, double* __restrict__ P) {
+  extern __shared__ double r11[];   // kk x kk
+  __shared__ int Js[kLMax];
+  const int kk = *kout;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) Js[e] = J[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) {
+    const int tt = e / kk, u = e % kk;
+    r11[e] = R[(int64_t)tt * n + Js[u]];
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int cp = colpos[j];
+  if (cp >= 0) {
+    for (int tt = 0; tt < k; ++tt) P[(int64_t)tt * n + j] = (tt == cp) ? 1.0 : 0.0;
+    return;
+  }
+  for (int tt = kk; tt < k; ++tt) P[(int64_t)tt * n + j] = 0.0;
+  for (int tt = kk - 1; tt >= 0; --tt) {
+    double x = R[(int64_t)tt * n + j];
+    for (int u = tt + 1; u < kk; ++u) x -= r11[tt * kk + u] * P[(int64_t)u * n + j];
+    P[(int64_t)tt * n + j] = x / r11[tt * kk + tt];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
+                              double* R, int* J, int* colpos, int* kout, cudaStream_t st) {
+  if (n > NT * QMAX || rows > kLMax) return cudaErrorInvalidValue;
+  cpqr_small_kernel<<<1, NT, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J, colpos, kout);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
+                           int k, int n, double* P, cudaStream_t st) {
+  const int nt = 256;
+  const size_t sm = sizeof(double) * (size_t)k * k;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(solve_p_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  solve_p_kernel<<<(n + nt - 1) / nt, nt, sm, st>>>(R, J, colpos, kout, k, n, P);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace idsk

@@ -1,0 +1,181 @@
+// Internal declarations of the idsketch library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "idsketch.h"
+
+namespace idsk {
+
+// ------------------------------------------------------------------ limits
+constexpr int kLMax = 64;             // sketch width l (padded to 16 on device)
+constexpr int kMaxSegs = 64;          // column segments per sketch launch
+constexpr int kSimtWindowMax = 320;   // columns per SIMT sketch launch
+constexpr int kRecKMax = 64;          // rank handled by the error pass
+constexpr int kTableSize = 4096;
+
+// -------------------------------------------------- counter-based Gaussian
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with the round multipliers below; the key advances by the Weyl
+// increments after every round.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kStreamPsi = 1;
+constexpr uint32_t kStreamOmega = 2;
+
+#ifdef __CUDACC__
+__host__ __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                                  uint32_t& c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+}
+
+// Field f (bits 12f .. 12f+11) of the 128-bit block c0 | c1<<32 | c2<<64 | c3<<96.
+__host__ __device__ __forceinline__ uint32_t field12(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                     uint32_t c3, int f) {
+  const uint64_t lo = (uint64_t)c0 | ((uint64_t)c1 << 32);
+  const uint64_t hi = (uint64_t)c2 | ((uint64_t)c3 << 32);
+  const int b = 12 * f;
+  if (b + 12 <= 64) return (uint32_t)(lo >> b) & 0xFFFu;
+  if (b < 64) return (uint32_t)((lo >> b) | (hi << (64 - b))) & 0xFFFu;
+  return (uint32_t)(hi >> (b - 64)) & 0xFFFu;
+}
+
+// Ten consecutive entries G(index, 10*sb .. 10*sb+9) of stream `which`.
+__device__ __forceinline__ void gauss10(uint64_t index, uint32_t sb, uint32_t which, uint32_t k0,
+                                        uint32_t k1, const float* __restrict__ tab,
+                                        float out[10]) {
+  uint32_t c0 = (uint32_t)index, c1 = (uint32_t)(index >> 32), c2 = sb, c3 = which;
+  philox10(c0, c1, c2, c3, k0, k1);
+#pragma unroll
+  for (int f = 0; f < 10; ++f) out[f] = tab[field12(c0, c1, c2, c3, f)];
+}
+#endif
+
+// ------------------------------------------------------------- launch args
+struct Seg {
+  const void* ptr;   // first element of the segment's first column
+  int64_t ld;        // leading dimension (elements)
+  int32_t col0;      // first column of the segment inside the window
+  int32_t ncols;
+};
+
+struct Window {
+  int32_t nseg;
+  int32_t ncols;      // columns in the window
+  int64_t col_base;   // global index of the window's first column
+  Seg seg[kMaxSegs];
+};
+
+struct CoarseGeom {
+  int32_t on;
+  int32_t nx, ny, nz, sx, sy, sz, cx, cy, cz;   // c* = coarse points per direction
+  int64_t mc;
+};
+
+struct SketchArgs {
+  int64_t m;
+  int32_t l, lpad;
+  uint32_t k0, k1;
+  const float* table;   // 4096 quantiles (FP32, bf16-exact)
+  const float* omega;   // n_max x l, row-major
+  double* W;            // l x ldw, row-major (accumulated with atomics)
+  int64_t ldw;
+  void* Y;              // m x l, column-major, dtype
+  int32_t want_Y, y_accumulate;
+  void* Ac;             // mc x n_max, column-major, dtype
+  CoarseGeom cg;
+  int32_t bf16;         // round A to bfloat16 before the products
+};
+
+}  // namespace idsk
+
+// ------------------------------------------------------------------ handle
+struct id_sketch {
+  id_config cfg;
+  cudaStream_t st = nullptr;
+  int dev = 0, nsm = 0;
+  int64_t m = 0, n_max = 0, mc = 0;
+  int k = 0, l = 0, lpad = 0;
+  size_t esz = 4;
+  uint32_t key0 = 0, key1 = 0;
+  idsk::CoarseGeom cg{};
+
+  float* d_table = nullptr;
+  float* d_omega = nullptr;
+  double* d_W = nullptr;
+  void* d_Y = nullptr;
+  void* d_Ac = nullptr;
+
+  std::vector<idsk::Seg> pend;   // borrowed chunks, window-relative col0
+  int64_t pend_cols = 0;
+  int64_t n_seen = 0;            // columns accepted (launched + pending)
+  int64_t n_launched = 0;
+  bool y_started = false;
+  bool poisoned = false;
+
+  // factor workspace
+  double* d_work = nullptr;   // l x n_max copy of W
+  double* d_R = nullptr;      // max(k) x n_max
+  double* d_P = nullptr;      // k x n_max
+  int* d_J = nullptr;         // k
+  int* d_colpos = nullptr;    // n_max
+  int* d_kout = nullptr;      // 1
+  // coarse workspace (allocated on first id_coarse_factor)
+  double* d_V = nullptr;      // mc x k
+  double* d_F = nullptr;      // n_max x k
+  double* d_nu2 = nullptr;    // n_max
+  double* d_nu20 = nullptr;   // n_max
+  double* d_gpart = nullptr;  // coarse_blocks x (n_max + k)
+  double* d_upart = nullptr;  // coarse_blocks
+  double* d_cscal = nullptr;  // 8 scalars
+  int* d_cint = nullptr;      // 4 ints: pivot, stop, nrecompute, k_out
+  int* d_rlist = nullptr;     // n_max
+  double* d_Rc = nullptr;     // k x n_max
+  double* d_Pc = nullptr;     // k x n_max
+  int* d_Jc = nullptr;        // k
+  int* d_colposc = nullptr;   // n_max
+  int coarse_blocks = 0;
+  // error-pass workspace
+  double* d_part = nullptr;   // rec_blocks x 3
+  double* d_out3 = nullptr;   // 3
+  int* d_Jin = nullptr;       // kRecKMax
+  double* d_Pin = nullptr;    // kRecKMax x pin_cap
+  int64_t pin_cap = 0;
+  int rec_blocks = 0;
+};
+
+// ------------------------------------------------------------- launchers
+namespace idsk {
+cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64_t first,
+                                 int64_t count, int width, const float* table, float* out,
+                                 cudaStream_t st);
+cudaError_t launch_sketch_simt(const SketchArgs& a, const Window& w, int dtype, int nsm,
+                               cudaStream_t st);
+cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
+                              double* R, int* J, int* colpos, int* kout, cudaStream_t st);
+cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
+                           int k, int n, double* P, cudaStream_t st);
+cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
+cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
+                               const int* J, const double* P, int k, double* part, int nblk,
+                               double* out3, cudaStream_t st);
+void gaussian_table_host(float* vals, uint16_t* bits);
+void count_launches(int64_t n);
+}  // namespace idsk

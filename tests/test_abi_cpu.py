@@ -1,0 +1,89 @@
+"""The C ABI without a GPU: the library loads, exports every symbol declared
+in include/idsketch.h, and its host-only logic behaves (no GPU compute)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "idsketch.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_13257_gb300 import _binding, build
+    if not os.path.exists(_binding.LIB_PATH):
+        build.build()
+    return _binding.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(id_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13, names
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_1905_13257_gb300 import _binding
+    assert sorted(_binding.SIGNATURES) == names
+
+
+def test_config_struct_layout(lib):
+    from paper_1905_13257_gb300 import _binding
+    assert C.sizeof(_binding.IdConfig) == 96
+
+
+def test_gaussian_table_matches_oracle_bitwise(lib):
+    buf = (C.c_uint16 * 4096)()
+    assert lib.id_gaussian_table(buf) == 0
+    assert np.array_equal(np.array(buf[:], dtype=np.uint16), oracle.gaussian_table_bits())
+
+
+def test_status_strings_and_version(lib):
+    assert lib.id_status_str(0) == b"ok"
+    assert b"rank" in lib.id_status_str(5)
+    assert lib.id_version() >= 100
+
+
+def _cfg(**kw):
+    from paper_1905_13257_gb300 import _binding
+    c = _binding.IdConfig()
+    c.m, c.n_max, c.k, c.l, c.seed = 1000, 64, 4, 8, 1
+    for key, v in kw.items():
+        if key in ("grid", "coarse_stride"):
+            getattr(c, key)[:] = v
+        else:
+            setattr(c, key, v)
+    return c
+
+
+@pytest.mark.parametrize("bad", [dict(m=0), dict(n_max=0), dict(k=0), dict(k=9, l=8),
+                                 dict(l=65, k=4), dict(dtype=3), dict(prec=7),
+                                 dict(prec=1, dtype=1), dict(window_cols=-1),
+                                 dict(want_coarse=1, ncomp=3, grid=(10, 10, 10),
+                                      coarse_stride=(2, 2, 2)),  # 3000 != m
+                                 dict(want_coarse=1, ncomp=1, grid=(10, 10, 10),
+                                      coarse_stride=(0, 1, 1)),
+                                 dict(n_max=1 << 20)])
+def test_invalid_config_rejected_before_any_gpu_call(lib, bad):
+    h = C.c_void_p(123)
+    cfg = _cfg(**bad)
+    assert lib.id_sketch_create(C.byref(cfg), None, C.byref(h)) == 1
+    assert h.value is None
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.id_sketch_create(None, None, None) == 1
+    assert lib.id_sketch_stream_columns(None, None, 0, 0) == 1
+    assert lib.id_factor(None, None, None, None) == 1
+    assert lib.id_gaussian_fill(3, 0, 0, 1, 1, None, None) == 1
+    lib.id_sketch_destroy(None)

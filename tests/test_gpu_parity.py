@@ -1,0 +1,299 @@
+"""GPU parity: every step of the hot path through the C ABI against the oracle.
+
+Tolerances (spec bars, and the arithmetic behind the rest):
+  sketches W, Y   relative Frobenius <= 1e-5 for FP32 data (FP32-accurate
+                  products, FP64 accumulation of W); <= 1e-12 for FP64 data
+  skeleton J      identical whenever the oracle's pivot margin is >= 1e-4
+  P               from the same W: max |dP| <= 1e-9 * max(1, |P|) (FP64 QR on
+                  both sides); end to end: bounded by the W error x cond(R11)
+  errors          |rel_fro - oracle| <= 1e-4 * oracle + atol, atol = 2e-6 for
+                  FP32 data (FP32 reconstruction: ~sqrt(k) * 2^-24 relative per
+                  entry), 1e-12 for FP64 data
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synthetic import channel_field, low_rank_matrix, gaussian_matrix
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _sk(**kw):
+    from paper_1905_13257_gb300 import IdSketch
+    return IdSketch(**kw)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def stream(sk, A, chunks):
+    j = 0
+    for c in chunks:
+        sk.stream_columns(A[:, j:j + c])
+        j += c
+    assert j == A.shape[1]
+
+
+# ----------------------------------------------------------------- generator
+
+@pytest.mark.parametrize("which,first,count,width,seed", [
+    (1, 0, 1000, 60, 0), (1, 4_718_000, 592, 60, 0), (2, 0, 1000, 60, 0),
+    (1, 123, 77, 30, 0xDEADBEEF12345678), (2, 5, 9, 7, 3)])
+def test_gaussian_bitwise(which, first, count, width, seed):
+    from paper_1905_13257_gb300 import gaussian_fill
+    g = gaussian_fill(which, seed, first, count, width).cpu().double().numpy()
+    idx = np.arange(first, first + count)
+    if which == 1:
+        o = oracle.psi(width, 0, seed, rows=idx).T
+    else:
+        o = oracle.omega(0, width, seed, cols=idx)
+    assert np.array_equal(g, o)
+
+
+# ------------------------------------------------------------------ sketches
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.float64, 1e-12)])
+@pytest.mark.parametrize("grid,n,l,chunks,window", [
+    ((16, 12, 16), 100, 30, [32, 32, 32, 4], 0),        # ragged n, several launches
+    ((10, 7, 9), 37, 16, [37], 0),                      # m not a multiple of 64
+    ((16, 8, 16), 333, 60, [32] * 10 + [13], 96),       # borrowed windows of 96
+    ((8, 8, 8), 700, 64, [350, 350], 0),                # > one SIMT window (320)
+])
+def test_sketch_parity(dtype, tol, grid, n, l, chunks, window):
+    A = channel_field(grid, 3, n, seed=3, dtype=dtype, device=DEV)
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=n, k=min(8, l), l=l, seed=11, dtype=dtype, want_Y=True,
+             window_cols=window)
+    stream(sk, A, chunks)
+    W, Y, _ = sk.sketches()
+    An = A.cpu().double().numpy()
+    Wo, Yo = oracle.sketch(An, oracle.psi(l, m, 11), oracle.omega(n, l, 11))
+    assert rel(W.cpu().numpy(), Wo) <= tol
+    assert rel(Y.cpu().double().numpy(), Yo) <= tol
+    sk.close()
+
+
+def test_sketch_leading_dimension_and_separate_buffers():
+    m, n, l = 3000, 70, 20
+    base = gaussian_matrix(m + 17, n, seed=1, dtype=torch.float32, device=DEV)
+    A = base[:m]                            # lda = m + 17 > m
+    parts = [A[:, :30].clone(), A[:, 30:31].clone(), A[:, 31:]]   # three buffers
+    sk = _sk(m=m, n_max=n, k=5, l=l, seed=2, dtype=torch.float32, window_cols=64)
+    for p in parts:
+        sk.stream_columns(p)
+    W, Y, _ = sk.sketches()
+    Wo, Yo = oracle.sketch(A.cpu().double().numpy(), oracle.psi(l, m, 2), oracle.omega(n, l, 2))
+    assert rel(W.cpu().numpy(), Wo) <= 1e-5
+    assert rel(Y.cpu().double().numpy(), Yo) <= 1e-5
+    sk.close()
+
+
+def test_reset_and_restream():
+    A = channel_field((8, 8, 8), 3, 50, seed=1, dtype=torch.float32, device=DEV)
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=50, k=5, l=16, seed=4, dtype=torch.float32)
+    sk.stream_columns(A)
+    W1 = sk.sketches()[0].cpu().clone()
+    sk.reset()
+    sk.stream_columns(A[:, :25])
+    sk.stream_columns(A[:, 25:])
+    W2, Y2, _ = sk.sketches()
+    assert rel(W2.cpu().numpy(), W1.numpy()) <= 1e-12
+    sk.close()
+
+
+# ------------------------------------------------------------ randomized ID
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("grid,n,k,l", [((16, 12, 16), 120, 10, 20), ((8, 8, 8), 64, 20, 30),
+                                        ((12, 12, 12), 200, 16, 16), ((12, 12, 12), 200, 16, 26)])
+def test_factor_parity_gap_input(dtype, grid, n, k, l):
+    A = channel_field(grid, 3, n, seed=7, gap_k=k, dtype=dtype, device=DEV)
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=n, k=k, l=l, seed=9, dtype=dtype)
+    stream(sk, A, [32] * (n // 32) + ([n % 32] if n % 32 else []))
+    J, P, kout = sk.factor()
+    W = sk.sketches()[0].cpu().numpy()
+    An = A.cpu().double().numpy()
+    Wo, _ = oracle.sketch(An, oracle.psi(l, m, 9), oracle.omega(n, l, 9))
+    Jo, Po, ko, margin = oracle.column_id(Wo, k)
+    assert kout == ko == k
+    Pg = P.cpu().numpy()
+    assert np.array_equal(Pg[:, J.cpu().numpy()], np.eye(k))
+    if margin < 1e-4:      # pivots within rounding of a tie: J is not unique
+        pytest.skip(f"oracle pivot margin {margin:.1e} < 1e-4")
+    assert J.cpu().tolist() == Jo.tolist()
+    # same W on both sides: FP64 QR agreement
+    Jw, Pw, _, _ = oracle.column_id(W, k)
+    assert J.cpu().tolist() == Jw.tolist()
+    assert np.max(np.abs(Pg - Pw)) <= 1e-9 * max(1.0, np.max(np.abs(Pw)))
+    # end to end against the FP64 oracle
+    tolP = 1e-10 if dtype == torch.float64 else 1e-3
+    assert np.max(np.abs(Pg - Po)) <= tolP * max(1.0, np.max(np.abs(Po)))
+    sk.close()
+
+
+def test_factor_host_outputs_and_edge_ranks():
+    A = channel_field((8, 8, 8), 3, 40, seed=2, gap_k=8, dtype=torch.float64, device=DEV)
+    m = A.shape[0]
+    An = A.cpu().numpy()
+    for k, l, n in [(1, 10, 40), (8, 8, 40), (10, 10, 10), (16, 40, 40)]:
+        sk = _sk(m=m, n_max=n, k=k, l=l, seed=1, dtype=torch.float64)
+        sk.stream_columns(A[:, :n])
+        J, P, kout = sk.factor(device="cpu")
+        Wo, _ = oracle.sketch(An[:, :n], oracle.psi(l, m, 1), oracle.omega(n, l, 1))
+        Jo, Po, ko, margin = oracle.column_id(Wo, k)
+        assert kout == ko
+        if margin >= 1e-4:
+            assert J.tolist()[:kout] == Jo.tolist()
+        assert np.max(np.abs(P.numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+        sk.close()
+
+
+def test_rank_deficient_returns_kout():
+    from paper_1905_13257_gb300 import _binding as B
+    m, n, r = 2000, 60, 5
+    A = low_rank_matrix(m, n, r, seed=3, dtype=torch.float64, device=DEV)
+    A[:, 7] = 0.0
+    sk = _sk(m=m, n_max=n, k=12, l=20, seed=5, dtype=torch.float64)
+    sk.stream_columns(A)
+    J, P, kout = sk.factor()
+    Wo, _ = oracle.sketch(A.cpu().numpy(), oracle.psi(20, m, 5), oracle.omega(n, 20, 5))
+    Jo, Po, ko, _ = oracle.column_id(Wo, 12)
+    assert kout == ko == r
+    assert J.cpu().tolist()[r:] == [-1] * (12 - r)
+    assert 7 not in J.cpu().tolist()
+    fro, _ = sk.reconstruct_error(A, J[:r], P[:r])
+    assert fro <= 1e-12
+    sk.close()
+
+
+def test_zero_matrix():
+    m, n = 500, 20
+    A = torch.zeros((n, m), dtype=torch.float32, device=DEV).T
+    sk = _sk(m=m, n_max=n, k=3, l=8, seed=0, dtype=torch.float32)
+    sk.stream_columns(A)
+    J, P, kout = sk.factor()
+    assert kout == 0 and J.cpu().tolist() == [-1, -1, -1]
+    sk.close()
+
+
+# ---------------------------------------------------------- sub-sampled ID
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("grid,stride,n,k", [((16, 12, 16), (2, 2, 2), 90, 8),
+                                             ((20, 9, 13), (4, 2, 3), 70, 12),
+                                             ((8, 8, 8), (1, 1, 1), 40, 40)])
+def test_coarse_factor_parity(dtype, grid, stride, n, k):
+    nc = 3
+    A = channel_field(grid, nc, n, seed=5, gap_k=k, dtype=dtype, device=DEV)
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=n, k=k, l=max(k, 16), seed=1, dtype=dtype, grid=grid, ncomp=nc,
+             coarse_stride=stride, want_coarse=True, window_cols=64)
+    stream(sk, A, [32] * (n // 32) + ([n % 32] if n % 32 else []))
+    Jc, Pc, kout = sk.coarse_factor()
+    Ac = sk.sketches()[2].cpu().numpy()
+    rows = oracle.coarse_rows(grid, nc, stride)
+    An = A.cpu().double().numpy()
+    assert np.array_equal(Ac.astype(np.float64), An[rows])            # exact gather
+    Jo, Po, ko, margin = oracle.column_id(An[rows], k)
+    assert kout == ko
+    if margin >= 1e-4:
+        assert Jc.cpu().tolist()[:kout] == Jo.tolist()
+        assert np.max(np.abs(Pc.cpu().numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+    # lifted error (eq. eq:coarseregA) through the fused error pass
+    fro, mx = sk.reconstruct_error(A, Jc[:kout], Pc[:kout])
+    fo, mo = oracle.recon_error(An, Jo, Po)
+    atol = 2e-6 if dtype == torch.float32 else 1e-12
+    assert abs(fro - fo) <= 1e-4 * fo + atol
+    sk.close()
+
+
+def test_coarse_rank_deficient():
+    grid, nc = (8, 8, 8), 1
+    m, n, r = 512, 30, 4
+    A = low_rank_matrix(m, n, r, seed=8, dtype=torch.float64, device=DEV)
+    sk = _sk(m=m, n_max=n, k=10, l=16, seed=1, dtype=torch.float64, grid=grid, ncomp=nc,
+             coarse_stride=(2, 1, 1), want_coarse=True)
+    sk.stream_columns(A)
+    Jc, Pc, kout = sk.coarse_factor()
+    rows = oracle.coarse_rows(grid, nc, (2, 1, 1))
+    Jo, Po, ko, _ = oracle.column_id(A.cpu().numpy()[rows], 10)
+    assert kout == ko == r
+    sk.close()
+
+
+# ------------------------------------------------------------- error pass
+
+@pytest.mark.parametrize("dtype,atol", [(torch.float32, 2e-6), (torch.float64, 1e-12)])
+@pytest.mark.parametrize("m,n,k", [(6000, 100, 10), (4097, 33, 1), (64 * 7 + 5, 250, 64)])
+def test_recon_error_parity(dtype, atol, m, n, k):
+    A = gaussian_matrix(m, n, seed=m, dtype=dtype, device=DEV)
+    A = A + low_rank_matrix(m, n, 4, seed=1, dtype=dtype, device=DEV) * 10
+    A[5, 3] = 0.0   # skipped by the entry-wise metric
+    g = np.random.default_rng(n)
+    J = torch.tensor(g.choice(n, size=k, replace=False), dtype=torch.int32)
+    P = torch.tensor(g.normal(size=(k, n)) * 0.3)
+    sk = _sk(m=m, n_max=n, k=min(k, 64), l=64, seed=0, dtype=dtype)
+    fro, mx = sk.reconstruct_error(A, J, P)
+    fo, mo = oracle.recon_error(A.cpu().double().numpy(), J.numpy(), P.numpy())
+    assert abs(fro - fo) <= 1e-4 * fo + atol
+    assert abs(mx - mo) <= 1e-4 * mo + atol
+    # device-resident J and P give the same numbers
+    fro2, mx2 = sk.reconstruct_error(A, J.to(DEV), P.to(DEV))
+    assert fro2 == fro and mx2 == mx
+    sk.close()
+
+
+def test_recon_error_invalid_arguments():
+    from paper_1905_13257_gb300 import IdError
+    A = gaussian_matrix(100, 10, seed=1, dtype=torch.float32, device=DEV)
+    sk = _sk(m=100, n_max=10, k=2, l=4, seed=0, dtype=torch.float32)
+    with pytest.raises(IdError):
+        sk.reconstruct_error(A, torch.tensor([0, 10], dtype=torch.int32), torch.zeros(2, 10))
+    with pytest.raises(IdError):
+        sk.stream_columns(gaussian_matrix(100, 11, 1, torch.float32, DEV))   # > n_max
+    sk.close()
+
+
+def test_factor_before_columns_is_state_error():
+    from paper_1905_13257_gb300 import IdError
+    sk = _sk(m=100, n_max=10, k=2, l=4, seed=0, dtype=torch.float32)
+    with pytest.raises(IdError) as e:
+        sk.factor()
+    assert e.value.status == 2
+    with pytest.raises(IdError) as e:
+        sk.coarse_factor()
+    assert e.value.status == 2
+    sk.close()
+
+
+def test_allocation_cap_injects_oom(monkeypatch):
+    from paper_1905_13257_gb300 import IdError
+    monkeypatch.setenv("IDSKETCH_ALLOC_CAP_BYTES", "1000")
+    with pytest.raises(IdError) as e:
+        _sk(m=10000, n_max=100, k=4, l=8, seed=0, dtype=torch.float32)
+    assert e.value.status == 3
+
+
+# ------------------------------------------------------- precision form (BF16)
+
+def test_bf16_sketch_matches_oracle_on_rounded_data():
+    A = channel_field((16, 12, 16), 3, 64, seed=2, dtype=torch.float32, device=DEV)
+    m, n, l = A.shape[0], 64, 30
+    sk = _sk(m=m, n_max=n, k=10, l=l, seed=3, dtype=torch.float32, prec="bf16")
+    sk.stream_columns(A)
+    W, Y, _ = sk.sketches()
+    Ab = A.to(torch.bfloat16).double().cpu().numpy()
+    Wo, Yo = oracle.sketch(Ab, oracle.psi(l, m, 3), oracle.omega(n, l, 3))
+    assert rel(W.cpu().numpy(), Wo) <= 1e-5
+    assert rel(Y.cpu().double().numpy(), Yo) <= 1e-5
+    sk.close()
