@@ -152,6 +152,29 @@ id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64
                                const int32_t* J, const double* P, int32_t k,
                                double* rel_fro, double* rel_max);
 
+/* Largest k * n of P that id_reconstruct_error_noalloc accepts. */
+#define ID_NOALLOC_MAX_KN 131072
+
+/* The error pass of id_reconstruct_error for callers that must not allocate
+ * device memory.  No counterpart in the paper: it exists for users whose own
+ * allocator already holds the device's memory, who work to a fixed memory
+ * budget, or who cannot accept the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply.  It needs no handle.  Inputs and outputs are as
+ * in id_reconstruct_error; m is the number of rows and dtype the id_dtype of
+ * A.  All scratch (per-CTA partial sums, result scalars, copies of J and P)
+ * lives in one fixed device array of about 1.1 MB that every GPU loading the
+ * library holds until the process exits.  The call allocates nothing.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the array's device address; make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU race.  Synchronises cuda_stream before returning.
+ * Errors: ID_ERR_INVALID_ARG for the cases of id_reconstruct_error, a bad
+ * dtype, or k * n > ID_NOALLOC_MAX_KN (the array's capacity for P). */
+id_status id_reconstruct_error_noalloc(const void* d_A, int64_t lda, int64_t m, int64_t n,
+                                       int32_t dtype, const int32_t* J, const double* P,
+                                       int32_t k, double* rel_fro, double* rel_max,
+                                       void* cuda_stream);
+
 /* Borrow the device buffers of the sketch (valid until reset/destroy):
  *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])
  *   Y  m x l, dtype, column-major (entry (i, s) at Y[i + s*m]); NULL unless want_Y

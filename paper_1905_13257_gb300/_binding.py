@@ -25,6 +25,7 @@ ID_F64 = 1
 ID_SKETCH_EXACT = 0
 ID_SKETCH_BF16 = 1
 ID_RANK_TOL_FACTOR = 64.0
+ID_NOALLOC_MAX_KN = 131072
 
 
 class IdConfig(C.Structure):
@@ -57,6 +58,10 @@ SIGNATURES = {
     "id_reconstruct_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                        C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                        C.POINTER(C.c_double)]),
+    "id_reconstruct_error_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                               C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                               C.c_void_p]),
     "id_sketch_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
