@@ -219,7 +219,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     lib = load()
 
-    grid = GRID
+    grid = tuple(int(x) for x in args.grid.split(",")) if args.grid else GRID
     cfgd = workload(grid, args.n)
     m, n = cfgd["m"], cfgd["n"]
     A = channel_field(grid, NCOMP, n, seed=SEED + rank, dtype=torch.float32, device=dev)
@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=NSNAP)
+    ap.add_argument("--grid", type=str, default=None,
+                    help="nx,ny,nz of a smaller case (profiling); default 128,96,128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
