@@ -204,6 +204,10 @@ id_status id_gaussian_table(uint16_t out[4096]);
  * handles, all devices); for accounting in benchmarks. */
 int64_t id_kernel_launches(void);
 
+/* Text of the last CUDA error behind an ID_ERR_CUDA status in this process
+ * ("no error" if none). */
+const char* id_last_cuda_error(void);
+
 /* Static string for a status code. */
 const char* id_status_str(id_status s);
 

@@ -70,6 +70,7 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p]),
     "id_gaussian_table": (C.c_int, [C.POINTER(C.c_uint16)]),
     "id_kernel_launches": (C.c_int64, []),
+    "id_last_cuda_error": (C.c_char_p, []),
     "id_status_str": (C.c_char_p, [C.c_int]),
     "id_version": (C.c_int32, []),
 }
@@ -98,7 +99,10 @@ def load():
 class IdError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        msg = load().id_status_str(status).decode()
+        lib = load()
+        msg = lib.id_status_str(status).decode()
+        if status == ID_ERR_CUDA:
+            msg += f" [{lib.id_last_cuda_error().decode()}]"
         super().__init__(f"{where}: {msg} (status {status})")
 
 

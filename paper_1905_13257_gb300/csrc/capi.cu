@@ -18,6 +18,7 @@ namespace idsk {
 int coarse_blocks_needed(int64_t mc, int nsm);
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_last_cuda_error{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }
 
@@ -87,7 +88,7 @@ void free_all(id_sketch* h) {
   void* ptrs[] = {h->d_omega, h->d_W, h->d_Y, h->d_Ac, h->d_work, h->d_R, h->d_P, h->d_J,
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gpart,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
-                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin};
+                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -115,21 +116,32 @@ id_status validate(const id_config* c) {
   return ID_OK;
 }
 
-#define IDSK_CUDA(h, expr)                \
-  do {                                    \
-    cudaError_t e_ = (expr);              \
-    if (e_ != cudaSuccess) {              \
-      (h)->poisoned = true;               \
-      return ID_ERR_CUDA;                 \
-    }                                     \
+#define IDSK_CUDA(h, expr)                 \
+  do {                                     \
+    cudaError_t e_ = (expr);               \
+    if (e_ != cudaSuccess) {               \
+      g_last_cuda_error.store((int)e_);    \
+      (h)->poisoned = true;                \
+      return ID_ERR_CUDA;                  \
+    }                                      \
   } while (0)
+
+// Tensor-core sketch: FP32 data whose pending columns all start on 16-byte
+// boundaries (128-bit loads); everything else takes the SIMT kernel.
+bool use_tc(const id_sketch* h) {
+  if (h->cfg.dtype != ID_F32 || h->sketch_kernel == 2) return false;
+  for (const Seg& s : h->pend)
+    if (((uintptr_t)s.ptr & 15u) != 0 || (s.ld & 3) != 0) return false;
+  return true;
+}
 
 id_status launch_pending(id_sketch* h) {
   while (!h->pend.empty()) {
     Window w;
     memset(&w, 0, sizeof(w));
     w.col_base = h->n_launched;
-    const int wmax = kSimtWindowMax;
+    const bool tc = use_tc(h);
+    const int wmax = tc ? kTcMaxTiles * 128 : kSimtWindowMax;
     int taken = 0;
     size_t consumed = 0;
     while (consumed < h->pend.size() && w.nseg < kMaxSegs && taken < wmax) {
@@ -167,7 +179,12 @@ id_status launch_pending(id_sketch* h) {
     a.Ac = h->d_Ac;
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
-    IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, h->nsm, h->st));
+    if (tc) {
+      IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, h->nsm, h->drain_blocks, h->d_status,
+                                    h->st));
+    } else {
+      IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, h->nsm, h->st));
+    }
     h->y_started = true;
     h->n_launched += taken;
   }
@@ -202,6 +219,10 @@ const char* id_status_str(id_status s) {
 int32_t id_version(void) { return 100; }
 
 int64_t id_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* id_last_cuda_error(void) {
+  return cudaGetErrorString((cudaError_t)g_last_cuda_error.load());
+}
 
 id_status id_gaussian_table(uint16_t out[4096]) {
   if (!out) return ID_ERR_INVALID_ARG;
@@ -265,9 +286,15 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
     delete h;
     return ID_ERR_CUDA;
   }
+  if (const char* e = getenv("IDSKETCH_SKETCH")) {
+    if (!strcmp(e, "tc")) h->sketch_kernel = 1;
+    if (!strcmp(e, "simt")) h->sketch_kernel = 2;
+  }
+  if (const char* e = getenv("IDSKETCH_DRAIN_BLOCKS")) h->drain_blocks = std::max(1, atoi(e));
   const int64_t nm = h->n_max;
   const int k = h->k, l = h->l;
   Allocator al;
+  al.get(&h->d_status, 1);
   al.get(&h->d_omega, (size_t)nm * l);
   al.get(&h->d_W, (size_t)l * nm);
   if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);
@@ -306,6 +333,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   cudaError_t e = launch_gaussian_fill(kStreamOmega, h->key0, h->key1, 0, nm, l, h->d_table,
                                        h->d_omega, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_W, 0, sizeof(double) * l * nm, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) {
     free_all(h);
@@ -378,9 +406,14 @@ id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out) {
   IDSK_CUDA(h, launch_solve_p(h->d_R, h->d_J, h->d_colpos, h->d_kout, k, (int)n, h->d_P, h->st));
   if ((s = copy_out(h, J, h->d_J, sizeof(int32_t) * k)) != ID_OK) return s;
   if ((s = copy_out(h, P, h->d_P, sizeof(double) * k * n)) != ID_OK) return s;
-  int32_t kk = 0;
+  int32_t kk = 0, dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_kout, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(&dst, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
   IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (dst) {
+    h->poisoned = true;
+    return ID_ERR_TIMEOUT;
+  }
   if (k_out) *k_out = kk;
   return kk < k ? ID_ERR_RANK_DEFICIENT : ID_OK;
 }
@@ -397,10 +430,15 @@ id_status id_coarse_factor(id_sketch* h, int32_t* Jc, double* Pc, int32_t* k_out
   IDSK_CUDA(h, launch_coarse_cpqr(h, n, h->st));
   if ((s = copy_out(h, Jc, h->d_Jc, sizeof(int32_t) * k)) != ID_OK) return s;
   if ((s = copy_out(h, Pc, h->d_Pc, sizeof(double) * k * n)) != ID_OK) return s;
-  int32_t kk = 0;
+  int32_t kk = 0, dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_cint + 3, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(&dst, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
   IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (dst) {
+    h->poisoned = true;
+    return ID_ERR_TIMEOUT;
+  }
   if (k_out) *k_out = kk;
   return kk < k ? ID_ERR_RANK_DEFICIENT : ID_OK;
 }

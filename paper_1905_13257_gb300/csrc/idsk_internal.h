@@ -14,6 +14,7 @@ namespace idsk {
 constexpr int kLMax = 64;             // sketch width l (padded to 16 on device)
 constexpr int kMaxSegs = 64;          // column segments per sketch launch
 constexpr int kSimtWindowMax = 320;   // columns per SIMT sketch launch
+constexpr int kTcMaxTiles = 4;        // 128-column tiles per tensor-core launch (TMEM budget)
 constexpr int kRecKMax = 64;          // rank handled by the error pass
 constexpr int kTableSize = 4096;
 
@@ -129,6 +130,9 @@ struct id_sketch {
   int64_t n_launched = 0;
   bool y_started = false;
   bool poisoned = false;
+  int sketch_kernel = 0;         // 0 auto, 1 tensor cores, 2 SIMT (IDSKETCH_SKETCH)
+  int drain_blocks = 8;          // row blocks between FP64 flushes of W^T (tensor cores)
+  int* d_status = nullptr;       // nonzero: a bounded device wait gave up
 
   // factor workspace
   double* d_work = nullptr;   // l x n_max copy of W
@@ -168,6 +172,8 @@ cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64
                                  cudaStream_t st);
 cudaError_t launch_sketch_simt(const SketchArgs& a, const Window& w, int dtype, int nsm,
                                cudaStream_t st);
+cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
+                             int drain_blocks, int* status, cudaStream_t st);
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
                               double* R, int* J, int* colpos, int* kout, cudaStream_t st);
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,

@@ -1,0 +1,556 @@
+// Fused single-read sketch on the tcgen05 tensor cores (FP32 data).
+//
+// One read of each 128 x 128 tile of A forms both randomized sketches of the
+// window's columns (Algorithm 4 step 3, transposed orientation; eq.
+// eq:sampmatrix) and gathers the coarse-grid rows of Algorithm 5 step 3:
+//   W^T(c, :) += A(R, c)^T Psi(:, R)^T   (128 columns x 64, TMEM accumulator)
+//   Y(R, :)   += A(R, C) Omega(C, :)     (128 rows x 64, TMEM accumulator)
+//
+// Precision.  A (FP32) is split once per tile into NP bfloat16 pieces,
+// A = a0 + a1 (+ rounding below 2^-16 |A|); Psi and Omega are exact in
+// bfloat16 (quantile table), so every tensor-core product is exact and the
+// sketches carry only the split error (about 2.4e-6 relative in Frobenius
+// norm for NP = 2) and the FP32 accumulation.  NP = 1 is the bfloat16
+// precision form.  W^T partials are flushed to FP64 in global memory every
+// few row blocks.
+//
+// Shared-memory layout.  A piece tile is stored in 128-byte-swizzled 1 KB
+// atoms of 8 columns x 64 rows (rows contiguous).  Read as K-major it is the
+// A operand of the W^T product (M = columns, K = rows); read as MN-major it is
+// the A operand of the Y product (M = rows, K = columns): one copy serves both
+// products.  Psi(:, R)^T and Omega(C, :)^T are K-major B operands.
+//
+// Warp roles (one CTA per SM, persistent over a contiguous range of row
+// blocks):
+//   warps 0-15   converters: load A with 128-bit coalesced loads (two tiles in
+//                flight, held in registers), split into pieces, store them to
+//                the swizzled piece buffer (double-buffered), gather coarse rows
+//   warps 16-19  epilogue: draw Psi for upcoming row blocks (counter
+//                generator), drain Y to global memory, flush W^T to FP64
+//   warp 20      TMEM allocation and the single-thread tcgen05.mma issue
+// Every mbarrier wait is bounded: on timeout the CTA raises an abort flag,
+// every role leaves its loop, in-flight MMAs are waited for (bounded) and the
+// TMEM is freed; the host reads the status word and reports ID_ERR_TIMEOUT.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "idsk_internal.h"
+
+namespace idsk {
+namespace {
+
+constexpr int TR = 128;                 // rows per tile
+constexpr int TCOLS = 128;              // columns per tile
+constexpr int NCONV = 16;               // converter warps
+constexpr int NEPI = 4;                 // epilogue warps
+constexpr int MMA_WARP = NCONV + NEPI;  // 20
+constexpr int NTHREADS = (NCONV + NEPI + 1) * 32;
+constexpr int LP = 64;                  // padded sketch width: N of both products
+constexpr uint32_t PIECE_BYTES = TR * TCOLS * 2;     // 32 KB
+constexpr uint32_t PSI_BYTES = LP * TR * 2;          // 16 KB
+constexpr uint32_t OMEGA_TILE_BYTES = LP * TCOLS * 2;  // 16 KB
+constexpr int TMEM_COLS = 512;
+constexpr int TMEM_Y = kTcMaxTiles * LP;             // Y accumulators after W^T
+constexpr long long kWaitCycles = 4000000000LL;      // ~2 s: a wait this long is a bug
+
+// barrier slots
+enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE1,
+       B_YF0, B_YF1, B_YE0, B_YE1, B_WF, B_WE, B_DONE, NBAR };
+
+struct Smem {
+  uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES]
+  uint32_t omega;    // [kTcMaxTiles][OMEGA_TILE_BYTES]
+  uint32_t psi;      // [2][PSI_BYTES]
+  uint32_t bars;     // NBAR x 8 bytes
+  uint32_t tmem_slot;
+  uint32_t abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ int ld_volatile_shared(uint32_t a) {
+  int v;
+  asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_volatile_shared(uint32_t a, int v) {
+  asm volatile("st.volatile.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Bounded wait on a phase of an mbarrier; false (and the abort flag raised) on
+// timeout or when another role already aborted.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 15) == 15) {
+      if (ld_volatile_shared(abort_flag)) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        st_volatile_shared(abort_flag, 1);
+        return false;
+      }
+      __nanosleep(32);
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte
+// offsets, descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t IDESC_W = idesc_bf16(128, LP, 0);   // A^T K-major (K = rows)
+constexpr uint32_t IDESC_Y = idesc_bf16(128, LP, 1);   // A MN-major (M = rows)
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Byte offset of element (mn, k) in a K-major 128B-swizzled operand whose
+// 8-row groups are `sbo` bytes apart and whose two 64-wide K halves are 1 KB
+// apart (tile of up to 128 x 128 bf16, atoms (mn/8, k/64) at (mn/8)*sbo +
+// (k/64)*1024).
+__device__ __forceinline__ uint32_t swz(uint32_t mn, uint32_t k, uint32_t sbo) {
+  return (mn >> 3) * sbo + (k >> 6) * 1024u + (mn & 7u) * 128u +
+         ((((k & 63u) >> 3) ^ (mn & 7u)) << 4) + (k & 7u) * 2u;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void st_shared_v2(uint32_t a, uint32_t x, uint32_t y) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y) : "memory");
+}
+
+__device__ __forceinline__ void st_shared_u16(uint32_t a, uint16_t v) {
+  asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+
+__device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
+  const int64_t i = r % g.nx;
+  const int64_t rest = r / g.nx;
+  const int64_t z = rest % g.nz;
+  const int64_t rest2 = rest / g.nz;
+  const int64_t j = rest2 % g.ny;
+  const int64_t c = rest2 / g.ny;
+  if (i % g.sx || j % g.sy || z % g.sz) return -1;
+  return ((c * g.cy + j / g.sy) * g.cz + z / g.sz) * g.cx + i / g.sx;
+}
+
+__device__ __forceinline__ const float* column_ptr(const Window& w, int c) {
+  for (int s = 0; s < w.nseg; ++s) {
+    const Seg& sg = w.seg[s];
+    if (c >= sg.col0 && c < sg.col0 + sg.ncols)
+      return reinterpret_cast<const float*>(sg.ptr) + (int64_t)(c - sg.col0) * sg.ld;
+  }
+  return nullptr;
+}
+
+// 8 columns x 4 rows of one tile for one converter thread
+template <int NP>
+__device__ __forceinline__ void load_tile(const SketchArgs& a, const Window& w, int64_t r0,
+                                          int ct, int col_off, float4 (&v)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = ct * TCOLS + col_off + j;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c < w.ncols) {
+      const float* p = column_ptr(w, c);
+      if (r0 + 3 < a.m) {
+        x = __ldcs(reinterpret_cast<const float4*>(p + r0));
+      } else {
+        if (r0 < a.m) x.x = p[r0];
+        if (r0 + 1 < a.m) x.y = p[r0 + 1];
+        if (r0 + 2 < a.m) x.z = p[r0 + 2];
+      }
+    }
+    v[j] = x;
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Window w, int drain_blocks, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  Smem S;
+  S.pieces = base;
+  S.omega = S.pieces + 2u * NP * PIECE_BYTES;
+  S.psi = S.omega + kTcMaxTiles * OMEGA_TILE_BYTES;
+  S.bars = S.psi + 2u * PSI_BYTES;
+  S.tmem_slot = S.bars + NBAR * 8u;
+  S.abort_flag = S.tmem_slot + 4u;
+  auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nct = (w.ncols + TCOLS - 1) / TCOLS;
+  const int64_t nrb = (a.m + TR - 1) / TR;
+  const int64_t rb_begin = nrb * blockIdx.x / gridDim.x;
+  const int64_t rb_end = nrb * (blockIdx.x + 1) / gridDim.x;
+  const int nloc = (int)(rb_end - rb_begin);
+  const int ntile = nloc * nct;
+
+  if (tid == 0) {
+    mbar_init(bar(B_FULL0), NCONV);
+    mbar_init(bar(B_FULL1), NCONV);
+    mbar_init(bar(B_FREE0), 1);
+    mbar_init(bar(B_FREE1), 1);
+    mbar_init(bar(B_PSIF0), NEPI);
+    mbar_init(bar(B_PSIF1), NEPI);
+    mbar_init(bar(B_PSIE0), 1);
+    mbar_init(bar(B_PSIE1), 1);
+    mbar_init(bar(B_YF0), 1);
+    mbar_init(bar(B_YF1), 1);
+    mbar_init(bar(B_YE0), NEPI);
+    mbar_init(bar(B_YE1), NEPI);
+    mbar_init(bar(B_WF), 1);
+    mbar_init(bar(B_WE), NEPI);
+    mbar_init(bar(B_DONE), 1);
+    st_volatile_shared(S.abort_flag, 0);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Omega(window, :) as a K-major bf16 B operand, resident for the kernel
+  for (int e = tid; e < kTcMaxTiles * TCOLS * LP; e += NTHREADS) {
+    const int s = e % LP, c = e / LP;
+    float v = 0.f;
+    if (s < a.l && c < w.ncols) v = a.omega[(w.col_base + c) * a.l + s];
+    st_shared_u16(S.omega + (uint32_t)(c >> 7) * OMEGA_TILE_BYTES + swz(s, c & 127, 2048u),
+                  bf16_bits(v));
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     S.tmem_slot),
+                 "n"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
+
+  auto drain_due = [&](int i) { return ((i + 1) % drain_blocks) == 0 || i == nloc - 1; };
+
+  if (warp < NCONV) {
+    // ------------------------------------------------------------ converters
+    const int col_off = warp * 8;
+    const int row_off = lane * 4;
+    float4 cur[8], nxt[8];
+    int64_t rc[4] = {-1, -1, -1, -1};
+    if (ntile > 0) load_tile<NP>(a, w, (rb_begin)*TR + row_off, 0, col_off, cur);
+    for (int t = 0; t < ntile; ++t) {
+      const int i = t / nct, ct = t - i * nct;
+      const int64_t r0 = (rb_begin + i) * TR + row_off;
+      if (t + 1 < ntile) {
+        const int i1 = (t + 1) / nct, ct1 = (t + 1) - i1 * nct;
+        load_tile<NP>(a, w, (rb_begin + i1) * TR + row_off, ct1, col_off, nxt);
+      }
+      if (ct == 0 && a.cg.on) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rc[q] = (r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
+      }
+      const int b = t & 1;
+      if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) break;
+      const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 x = cur[j];
+        const uint32_t off = swz((uint32_t)(col_off + j), (uint32_t)row_off, 2048u);
+        const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
+        st_shared_v2(pbuf + off, h01, h23);
+        if (NP > 1) {
+          const float2 f01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h01));
+          const float2 f23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h23));
+          st_shared_v2(pbuf + PIECE_BYTES + off, pack_bf16x2(x.x - f01.x, x.y - f01.y),
+                       pack_bf16x2(x.z - f23.x, x.w - f23.y));
+        }
+        if (a.cg.on) {
+          const int c = ct * TCOLS + col_off + j;
+          if (c < w.ncols) {
+            float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + c);
+            if (rc[0] >= 0) Ac[rc[0]] = x.x;
+            if (rc[1] >= 0) Ac[rc[1]] = x.y;
+            if (rc[2] >= 0) Ac[rc[2]] = x.z;
+            if (rc[3] >= 0) Ac[rc[3]] = x.w;
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_FULL0 + b));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+    }
+  } else if (warp < MMA_WARP) {
+    // -------------------------------------------------------------- epilogue
+    const int q = warp - NCONV;           // TMEM lane quarter
+    const int rl = q * 32 + lane;         // row (Y) / column (W^T) inside the tile
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    auto gen_psi = [&](int i, int pb) {
+      const int64_t r = (rb_begin + i) * TR + rl;
+      const uint32_t dst = S.psi + (uint32_t)pb * PSI_BYTES;
+      for (int sb = 0; sb * 10 < LP; ++sb) {
+        float g[10];
+        if (r < a.m) {
+          gauss10((uint64_t)r, (uint32_t)sb, kStreamPsi, a.k0, a.k1, a.table, g);
+        } else {
+#pragma unroll
+          for (int f = 0; f < 10; ++f) g[f] = 0.f;
+        }
+#pragma unroll
+        for (int f = 0; f < 10; ++f) {
+          const int s = sb * 10 + f;
+          if (s < LP) st_shared_u16(dst + swz((uint32_t)s, (uint32_t)rl, 2048u),
+                                    bf16_bits(s < a.l ? g[f] : 0.f));
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_PSIF0 + pb));
+    };
+    for (int i = 0; i < 2 && i < nloc; ++i) gen_psi(i, i);
+    int wd = 0;
+    for (int i = 0; i < nloc; ++i) {
+      const int pb = i & 1;
+      if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag)) break;
+      tc_fence_after();
+      {
+        const int64_t r = (rb_begin + i) * TR + rl;
+        float* Y = reinterpret_cast<float*>(a.Y);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(TMEM_Y + pb * LP + h * 32), v);
+          if (a.want_Y && r < a.m) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int s = h * 32 + j;
+              if (s < a.l) {
+                float* dst = Y + r + (int64_t)s * a.m;
+                *dst = a.y_accumulate ? *dst + v[j] : v[j];
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_YE0 + pb));
+      if (drain_due(i)) {
+        if (!mbar_wait(bar(B_WF), wd & 1, S.abort_flag)) break;
+        tc_fence_after();
+        for (int ct = 0; ct < nct; ++ct) {
+          const int c = ct * TCOLS + rl;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP + h * 32), v);
+            if (c < w.ncols) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int s = h * 32 + j;
+                if (s < a.l) atomicAdd(&a.W[(int64_t)s * a.ldw + w.col_base + c], (double)v[j]);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_WE));
+        ++wd;
+      }
+      if (i + 2 < nloc) {
+        if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag)) break;
+        gen_psi(i + 2, pb);
+      }
+    }
+  } else if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    uint32_t accw = 0;   // bit ct: W^T accumulator of tile ct holds data
+    int wd = 0;
+    int t = 0;
+    bool ok = true;
+    for (int i = 0; i < nloc && ok; ++i) {
+      const int pb = i & 1;
+      if (!mbar_wait(bar(B_PSIF0 + pb), (i >> 1) & 1, S.abort_flag)) break;
+      if (i >= 2 && !mbar_wait(bar(B_YE0 + pb), ((i >> 1) - 1) & 1, S.abort_flag)) break;
+      tc_fence_after();
+      const uint32_t psi_s = S.psi + (uint32_t)pb * PSI_BYTES;
+      const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + pb * LP);
+      for (int ct = 0; ct < nct; ++ct, ++t) {
+        const int b = t & 1;
+        if (!mbar_wait(bar(B_FULL0 + b), (t >> 1) & 1, S.abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
+        const uint32_t wtm = tmem + (uint32_t)(ct * LP);
+        const uint32_t om = S.omega + (uint32_t)ct * OMEGA_TILE_BYTES;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const uint32_t pa = pbuf + (uint32_t)p * PIECE_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {   // W^T: K = 16 rows per instruction
+            const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
+            const uint32_t acc = ((accw >> ct) & 1u) | (uint32_t)(p | kk);
+            mma_bf16(wtm, sdesc(pa + ko, 0u, 2048u), sdesc(psi_s + ko, 0u, 2048u), IDESC_W,
+                     acc);
+          }
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {   // Y: K = 16 columns per instruction
+            const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
+            const uint32_t acc = (uint32_t)(ct | p | kk);
+            mma_bf16(ytm, sdesc(pa + (uint32_t)kk * 4096u, 1024u, 2048u),
+                     sdesc(om + ko, 0u, 2048u), IDESC_Y, acc);
+          }
+        }
+        accw |= 1u << ct;
+        mma_commit(bar(B_FREE0 + b));
+      }
+      if (!ok) break;
+      mma_commit(bar(B_YF0 + pb));
+      mma_commit(bar(B_PSIE0 + pb));
+      if (drain_due(i)) {
+        mma_commit(bar(B_WF));
+        if (!mbar_wait(bar(B_WE), wd & 1, S.abort_flag)) break;
+        tc_fence_after();
+        ++wd;
+        accw = 0;
+      }
+    }
+    // every issued MMA has completed before the TMEM is released
+    mma_commit(bar(B_DONE));
+    const long long t0 = clock64();
+    while (!mbar_try(bar(B_DONE), 0)) {
+      if (clock64() - t0 > kWaitCycles) {
+        st_volatile_shared(S.abort_flag, 1);
+        break;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(TMEM_COLS)
+                 : "memory");
+  }
+  if (tid == 0 && ld_volatile_shared(S.abort_flag)) atomicOr(status, 1);
+}
+
+template <int NP>
+size_t tc_smem_bytes() {
+  return 1024 + 2u * NP * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES + 2u * PSI_BYTES +
+         NBAR * 8 + 16;
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
+                             int drain_blocks, int* status, cudaStream_t st) {
+  if (w.ncols <= 0) return cudaSuccess;
+  if (w.ncols > kTcMaxTiles * TCOLS || a.l > LP) return cudaErrorInvalidValue;
+  const int64_t nrb = (a.m + TR - 1) / TR;
+  const int grid = (int)std::min<int64_t>(nrb, nsm);
+  cudaError_t e;
+  if (npieces == 1) {
+    const size_t sm = tc_smem_bytes<1>();
+    e = cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+    if (e != cudaSuccess) return e;
+    sketch_tc_kernel<1><<<grid, NTHREADS, sm, st>>>(a, w, drain_blocks, status);
+  } else {
+    const size_t sm = tc_smem_bytes<2>();
+    e = cudaFuncSetAttribute(sketch_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+    if (e != cudaSuccess) return e;
+    sketch_tc_kernel<2><<<grid, NTHREADS, sm, st>>>(a, w, drain_blocks, status);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace idsk
