@@ -241,6 +241,11 @@ def run_ours(args):
             sk.stream_columns(A[:, j0:j0 + CHUNK])
         sk.flush()
         e1.record(stream)
+        if args.only == "sketch":
+            if record:
+                e1.synchronize()
+                phase_ms["sketch"] += e0.elapsed_time(e1)
+            return
         J, P, kout = sk.factor()
         e2.record(stream)
         Jc, Pc, kc = sk.coarse_factor()
@@ -285,22 +290,26 @@ def run_ours(args):
         dist.barrier()
     value = world * 4.0 * m * n / (ms / 1e3) / 1e9
 
-    # roofline of the dominant kernel (the fused sketch; one launch per step)
+    # roofline of the dominant kernel: the fused sketch (FP32 data takes the
+    # tensor-core kernel, 512 columns per launch).  Algorithmic bytes of one
+    # step: read A once, write A_c once, write Y once per launch plus one read
+    # of Y per later launch (read-modify-write across windows).
     per_phase = {k: v / args.steps for k, v in phase_ms.items()}
     peak, peak_kind = measured_peaks()
     mc = NCOMP * math.ceil(grid[0] / STRIDE[0]) * math.ceil(grid[1] / STRIDE[1]) * \
         math.ceil(grid[2] / STRIDE[2])
-    sketch_bytes = 4.0 * m * n + 4.0 * m * L_SKETCH + 4.0 * mc * n
-    launches_per_step = math.ceil(n / 320)
+    window = 512
+    launches_per_step = math.ceil(n / window)
+    sketch_bytes = 4.0 * m * n + 4.0 * mc * n + 4.0 * m * L_SKETCH * (2 * launches_per_step - 1)
     sketch_launch_ms = per_phase["sketch"] / launches_per_step
-    y_rmw = 8.0 * m * L_SKETCH * (launches_per_step - 1)
-    achieved = (sketch_bytes + y_rmw) / launches_per_step / (sketch_launch_ms / 1e3) / 1e9
-    roofline = {"kernel": "sketch_simt_kernel", "bound": "hbm", "achieved": achieved,
+    achieved = sketch_bytes / launches_per_step / (sketch_launch_ms / 1e3) / 1e9
+    roofline = {"kernel": "sketch_tc_kernel<2>", "bound": "hbm", "achieved": achieved,
                 "peak": peak, "peak_kind": f"of {peak_kind}", "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": kernel_traffic("sketch_simt.cu", "sketch_simt_kernel"),
-                "algorithmic_bytes_per_launch": (sketch_bytes + y_rmw) / launches_per_step,
-                "launch_ms": sketch_launch_ms, "phase_ms": per_phase}
+                "traffic": kernel_traffic("sketch_tc.cu", "sketch_tc_kernel<2>"),
+                "algorithmic_bytes_per_launch": sketch_bytes / launches_per_step,
+                "launch_ms": sketch_launch_ms, "launches_per_step": launches_per_step,
+                "phase_ms": per_phase}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -372,6 +381,8 @@ def main():
     ap.add_argument("--grid", type=str, default=None,
                     help="nx,ny,nz of a smaller case (profiling); default 128,96,128")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["all", "sketch"], default="all",
+                    help="profiling aid: 'sketch' runs only the streamed sketch per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
                     help="y-planes of component u in the CPU-baseline sample")

@@ -88,7 +88,7 @@ void free_all(id_sketch* h) {
   void* ptrs[] = {h->d_omega, h->d_W, h->d_Y, h->d_Ac, h->d_work, h->d_R, h->d_P, h->d_J,
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gpart,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
-                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status};
+                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -129,7 +129,7 @@ id_status validate(const id_config* c) {
 // Tensor-core sketch: FP32 data whose pending columns all start on 16-byte
 // boundaries (128-bit loads); everything else takes the SIMT kernel.
 bool use_tc(const id_sketch* h) {
-  if (h->cfg.dtype != ID_F32 || h->sketch_kernel == 2) return false;
+  if (h->cfg.dtype != ID_F32 || h->sketch_kernel == 2 || h->m < 128) return false;
   for (const Seg& s : h->pend)
     if (((uintptr_t)s.ptr & 15u) != 0 || (s.ld & 3) != 0) return false;
   return true;
@@ -179,6 +179,7 @@ id_status launch_pending(id_sketch* h) {
     a.Ac = h->d_Ac;
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
+    a.wpart = h->d_wpart;
     if (tc) {
       IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, h->nsm, h->drain_blocks, h->d_status,
                                     h->st));
@@ -295,6 +296,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   const int k = h->k, l = h->l;
   Allocator al;
   al.get(&h->d_status, 1);
+  if (cfg->dtype == ID_F32) al.get(&h->d_wpart, (size_t)h->nsm * kLMax * kTcMaxTiles * 128);
   al.get(&h->d_omega, (size_t)nm * l);
   al.get(&h->d_W, (size_t)l * nm);
   if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);

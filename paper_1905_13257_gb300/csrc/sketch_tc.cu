@@ -22,12 +22,15 @@
 //
 // Warp roles (one CTA per SM, persistent over a contiguous range of row
 // blocks):
-//   warps 0-15   converters: load A with 128-bit coalesced loads (two tiles in
-//                flight, held in registers), split into pieces, store them to
-//                the swizzled piece buffer (double-buffered), gather coarse rows
-//   warps 16-19  epilogue: draw Psi for upcoming row blocks (counter
+//   warps 0-7    converters: load A with 128-bit coalesced loads in half
+//                tiles (three register buffers: two half tiles in flight),
+//                split into pieces, store them to the swizzled piece buffer
+//                (double-buffered), gather coarse rows
+//   warps 8-11   epilogue: draw Psi for upcoming row blocks (counter
 //                generator), drain Y to global memory, flush W^T to FP64
-//   warp 20      TMEM allocation and the single-thread tcgen05.mma issue
+//   warp 12      TMEM allocation and the single-thread tcgen05.mma issue
+// 13 warps keep at most 4 warps per SM sub-partition, so a thread may hold
+// up to 128 registers.
 // Every mbarrier wait is bounded: on timeout the CTA raises an abort flag,
 // every role leaves its loop, in-flight MMAs are waited for (bounded) and the
 // TMEM is freed; the host reads the status word and reports ID_ERR_TIMEOUT.
@@ -42,9 +45,9 @@ namespace {
 
 constexpr int TR = 128;                 // rows per tile
 constexpr int TCOLS = 128;              // columns per tile
-constexpr int NCONV = 16;               // converter warps
+constexpr int NCONV = 8;                // converter warps
 constexpr int NEPI = 4;                 // epilogue warps
-constexpr int MMA_WARP = NCONV + NEPI;  // 20
+constexpr int MMA_WARP = NCONV + NEPI;  // 12
 constexpr int NTHREADS = (NCONV + NEPI + 1) * 32;
 constexpr int LP = 64;                  // padded sketch width: N of both products
 constexpr uint32_t PIECE_BYTES = TR * TCOLS * 2;     // 32 KB
@@ -53,6 +56,20 @@ constexpr uint32_t OMEGA_TILE_BYTES = LP * TCOLS * 2;  // 16 KB
 constexpr int TMEM_COLS = 512;
 constexpr int TMEM_Y = kTcMaxTiles * LP;             // Y accumulators after W^T
 constexpr long long kWaitCycles = 4000000000LL;      // ~2 s: a wait this long is a bug
+
+// Optional timeline of CTA 0 (clock64 stamps per role), compiled only when
+// IDSK_TC_TRACE is defined by a profiling harness.
+#ifdef IDSK_TC_TRACE
+__device__ long long g_tc_trace[4][8192];
+#define TC_TRACE(role, idx)                                              \
+  do {                                                                   \
+    if (blockIdx.x == 0 && (idx) < 8192) g_tc_trace[role][idx] = clock64(); \
+  } while (0)
+#else
+#define TC_TRACE(role, idx) \
+  do {                      \
+  } while (0)
+#endif
 
 // barrier slots
 enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE1,
@@ -101,18 +118,22 @@ __device__ __forceinline__ void st_volatile_shared(uint32_t a, int v) {
 }
 
 // Bounded wait on a phase of an mbarrier; false (and the abort flag raised) on
-// timeout or when another role already aborted.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag) {
+// timeout or when another role already aborted.  Between polls the thread
+// sleeps (sleep_ns), so that waiting roles leave the issue slots to the
+// converter warps that share their schedulers.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag,
+                          uint32_t sleep_ns = 64) {
+  if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
+    __nanosleep(sleep_ns);
     if (mbar_try(bar, parity)) return true;
-    if ((it & 15) == 15) {
+    if ((it & 7) == 7) {
       if (ld_volatile_shared(abort_flag)) return false;
       if (clock64() - t0 > kWaitCycles) {
         st_volatile_shared(abort_flag, 1);
         return false;
       }
-      __nanosleep(32);
     }
   }
 }
@@ -226,26 +247,19 @@ __device__ __forceinline__ const float* column_ptr(const Window& w, int c) {
   return nullptr;
 }
 
-// 8 columns x 4 rows of one tile for one converter thread
-template <int NP>
-__device__ __forceinline__ void load_tile(const SketchArgs& a, const Window& w, int64_t r0,
-                                          int ct, int col_off, float4 (&v)[8]) {
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int c = ct * TCOLS + col_off + j;
-    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < w.ncols) {
-      const float* p = column_ptr(w, c);
-      if (r0 + 3 < a.m) {
-        x = __ldcs(reinterpret_cast<const float4*>(p + r0));
-      } else {
-        if (r0 < a.m) x.x = p[r0];
-        if (r0 + 1 < a.m) x.y = p[r0 + 1];
-        if (r0 + 2 < a.m) x.z = p[r0 + 2];
-      }
-    }
-    v[j] = x;
+// The loaded value of column c, rows r0..r0+3, with out-of-range entries zero
+// (ragged last row block: the valid rows are read here, element by element).
+__device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window& w, int64_t r0,
+                                               int c, float4 x) {
+  if (r0 + 3 < a.m && c < w.ncols) return x;
+  float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c < w.ncols && r0 < a.m) {
+    const float* p = column_ptr(w, c) + r0;
+    y.x = p[0];
+    if (r0 + 1 < a.m) y.y = p[1];
+    if (r0 + 2 < a.m) y.z = p[2];
   }
+  return y;
 }
 
 template <int NP>
@@ -314,28 +328,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
 
   if (warp < NCONV) {
     // ------------------------------------------------------------ converters
-    const int col_off = warp * 8;
+    // A tile is two half tiles of 64 columns; each thread owns 8 columns x 4
+    // rows of a half tile.  The loads of the next half tile are issued before
+    // the current one is split and stored (ping-pong register buffers), with
+    // plain address arithmetic on the window's single segment when it has one.
     const int row_off = lane * 4;
-    float4 cur[8], nxt[8];
+    const bool one_seg = (w.nseg == 1);
+    const float* seg_base = reinterpret_cast<const float*>(w.seg[0].ptr);
+    const int64_t seg_ld = w.seg[0].ld;
     int64_t rc[4] = {-1, -1, -1, -1};
-    if (ntile > 0) load_tile<NP>(a, w, (rb_begin)*TR + row_off, 0, col_off, cur);
-    for (int t = 0; t < ntile; ++t) {
-      const int i = t / nct, ct = t - i * nct;
-      const int64_t r0 = (rb_begin + i) * TR + row_off;
-      if (t + 1 < ntile) {
-        const int i1 = (t + 1) / nct, ct1 = (t + 1) - i1 * nct;
-        load_tile<NP>(a, w, (rb_begin + i1) * TR + row_off, ct1, col_off, nxt);
-      }
-      if (ct == 0 && a.cg.on) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) rc[q] = (r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
-      }
-      const int b = t & 1;
-      if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) break;
-      const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
+    auto load_half = [&](int64_t r0, int c0, float4 (&v)[8]) {
+      const bool rows_ok = r0 + 3 < a.m;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const float4 x = cur[j];
+        const int c = c0 + j;
+        const float* p = seg_base;
+        if (rows_ok && c < w.ncols)
+          p = one_seg ? seg_base + (int64_t)c * seg_ld + r0 : column_ptr(w, c) + r0;
+        v[j] = __ldcs(reinterpret_cast<const float4*>(p));
+      }
+    };
+    auto store_half = [&](uint32_t pbuf, int64_t r0, int c0, int col_off,
+                          const float4 (&v)[8]) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 x = split_source(a, w, r0, c0 + j, v[j]);
         const uint32_t off = swz((uint32_t)(col_off + j), (uint32_t)row_off, 2048u);
         const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
         st_shared_v2(pbuf + off, h01, h23);
@@ -345,22 +362,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
           st_shared_v2(pbuf + PIECE_BYTES + off, pack_bf16x2(x.x - f01.x, x.y - f01.y),
                        pack_bf16x2(x.z - f23.x, x.w - f23.y));
         }
-        if (a.cg.on) {
-          const int c = ct * TCOLS + col_off + j;
-          if (c < w.ncols) {
-            float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + c);
-            if (rc[0] >= 0) Ac[rc[0]] = x.x;
-            if (rc[1] >= 0) Ac[rc[1]] = x.y;
-            if (rc[2] >= 0) Ac[rc[2]] = x.z;
-            if (rc[3] >= 0) Ac[rc[3]] = x.w;
-          }
+        if (a.cg.on && c0 + j < w.ncols) {
+          float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + c0 + j);
+          if (rc[0] >= 0) Ac[rc[0]] = x.x;
+          if (rc[1] >= 0) Ac[rc[1]] = x.y;
+          if (rc[2] >= 0) Ac[rc[2]] = x.z;
+          if (rc[3] >= 0) Ac[rc[3]] = x.w;
         }
       }
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_FULL0 + b));
+    };
+    const int c_lo = warp * 8;         // half 0 columns of this warp
+    const int c_hi = 64 + warp * 8;    // half 1 columns
+    float4 bufA[8], bufB[8];
+    if (ntile > 0) load_half(rb_begin * TR + row_off, c_lo, bufA);
+    int t = 0;
+    bool ok = true;
+    for (int i = 0; i < nloc && ok; ++i) {
+      const int64_t r0 = (rb_begin + i) * TR + row_off;
+      if (a.cg.on) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) cur[j] = nxt[j];
+        for (int q = 0; q < 4; ++q) rc[q] = (r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
+      }
+      for (int ct = 0; ct < nct; ++ct, ++t) {
+        const int cbase = ct * TCOLS;
+        load_half(r0, cbase + c_hi, bufB);                       // half 1 of this tile
+        const int b = t & 1;
+        if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) {
+          ok = false;
+          break;
+        }
+        const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
+        store_half(pbuf, r0, cbase + c_lo, c_lo, bufA);          // half 0
+        if (t + 1 < ntile) {                                      // half 0 of the next tile
+          const bool last_ct = (ct + 1 == nct);
+          load_half(last_ct ? r0 + TR : r0, last_ct ? c_lo : cbase + TCOLS + c_lo, bufA);
+        }
+        store_half(pbuf, r0, cbase + c_hi, c_hi, bufB);          // half 1
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_FULL0 + b));
+        if (warp == 0 && lane == 0) TC_TRACE(0, t);
+      }
     }
   } else if (warp < MMA_WARP) {
     // -------------------------------------------------------------- epilogue
@@ -393,7 +435,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
     int wd = 0;
     for (int i = 0; i < nloc; ++i) {
       const int pb = i & 1;
-      if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag)) break;
+      if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
       tc_fence_after();
       {
         const int64_t r = (rb_begin + i) * TR + rl;
@@ -403,35 +445,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
           float v[32];
           tmem_ld32(tmem + lane_base + (uint32_t)(TMEM_Y + pb * LP + h * 32), v);
           if (a.want_Y && r < a.m) {
+            float* yr = Y + r + (int64_t)(h * 32) * a.m;
+            if (a.y_accumulate) {   // all loads in flight before the stores
+              float old[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int s = h * 32 + j;
-              if (s < a.l) {
-                float* dst = Y + r + (int64_t)s * a.m;
-                *dst = a.y_accumulate ? *dst + v[j] : v[j];
-              }
+              for (int j = 0; j < 32; ++j)
+                old[j] = (h * 32 + j < a.l) ? __ldcs(yr + (int64_t)j * a.m) : 0.f;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] += old[j];
             }
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (h * 32 + j < a.l) __stcs(yr + (int64_t)j * a.m, v[j]);
           }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_YE0 + pb));
+      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i);
       if (drain_due(i)) {
-        if (!mbar_wait(bar(B_WF), wd & 1, S.abort_flag)) break;
+        if (!mbar_wait(bar(B_WF), wd & 1, S.abort_flag, 256)) break;
         tc_fence_after();
+        // W^T partials -> this CTA's private FP64 slab wpart[cta][s][c]
+        // (plain read-modify-write; the first flush of the launch stores)
+        double* slab = a.wpart + (int64_t)blockIdx.x * LP * (kTcMaxTiles * TCOLS);
         for (int ct = 0; ct < nct; ++ct) {
           const int c = ct * TCOLS + rl;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP + h * 32), v);
-            if (c < w.ncols) {
+            double* dst = slab + (int64_t)(h * 32) * (kTcMaxTiles * TCOLS) + c;
+            if (wd == 0) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int s = h * 32 + j;
-                if (s < a.l) atomicAdd(&a.W[(int64_t)s * a.ldw + w.col_base + c], (double)v[j]);
-              }
+              for (int j = 0; j < 32; ++j) dst[(int64_t)j * (kTcMaxTiles * TCOLS)] = (double)v[j];
+            } else {
+              double old[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) old[j] = dst[(int64_t)j * (kTcMaxTiles * TCOLS)];
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                dst[(int64_t)j * (kTcMaxTiles * TCOLS)] = old[j] + (double)v[j];
             }
           }
         }
@@ -440,10 +495,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
         if (lane == 0) mbar_arrive(bar(B_WE));
         ++wd;
       }
+      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 1);
       if (i + 2 < nloc) {
-        if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag)) break;
+        if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
         gen_psi(i + 2, pb);
       }
+      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 2);
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -464,6 +521,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
           ok = false;
           break;
         }
+        TC_TRACE(1, t);
         tc_fence_after();
         const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
         const uint32_t wtm = tmem + (uint32_t)(ct * LP);
@@ -521,6 +579,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
   if (tid == 0 && ld_volatile_shared(S.abort_flag)) atomicOr(status, 1);
 }
 
+// W(:, window) = sum over CTAs of their slabs, in CTA order (deterministic).
+// A CTA whose row range is empty never wrote its slab and is skipped.
+__global__ void wpart_reduce_kernel(const double* __restrict__ wpart, int nslab, int l, int ncols,
+                                    int64_t nrb, double* __restrict__ W, int64_t ldw,
+                                    int64_t col_base) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l * ncols) return;
+  const int s = e / ncols, c = e - s * ncols;
+  double acc = 0.0;
+  for (int b = 0; b < nslab; ++b) {
+    if (nrb * (b + 1) / nslab == nrb * b / nslab) continue;
+    acc += wpart[((int64_t)b * LP + s) * (kTcMaxTiles * TCOLS) + c];
+  }
+  W[(int64_t)s * ldw + col_base + c] = acc;
+}
+
 template <int NP>
 size_t tc_smem_bytes() {
   return 1024 + 2u * NP * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES + 2u * PSI_BYTES +
@@ -549,7 +623,12 @@ cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, 
     if (e != cudaSuccess) return e;
     sketch_tc_kernel<2><<<grid, NTHREADS, sm, st>>>(a, w, drain_blocks, status);
   }
-  count_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int tot = a.l * w.ncols;
+  wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(a.wpart, grid, a.l, w.ncols, nrb, a.W,
+                                                         a.ldw, w.col_base);
+  count_launches(2);
   return cudaGetLastError();
 }
 
