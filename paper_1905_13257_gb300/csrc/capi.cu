@@ -86,7 +86,7 @@ struct Allocator {
 
 void free_all(id_sketch* h) {
   void* ptrs[] = {h->d_omega, h->d_W, h->d_Y, h->d_Ac, h->d_work, h->d_R, h->d_P, h->d_J,
-                  h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gpart,
+                  h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gvec, h->d_hvec, h->d_vh, h->d_vl,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
                   h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart};
   for (void* p : ptrs)
@@ -317,7 +317,10 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
     al.get(&h->d_F, (size_t)nm * k);
     al.get(&h->d_nu2, (size_t)nm);
     al.get(&h->d_nu20, (size_t)nm);
-    al.get(&h->d_gpart, (size_t)h->coarse_blocks * (nm + kLMax));
+    al.get(&h->d_gvec, (size_t)8 * nm);       // row-split partials of A_c^T v_s
+    al.get(&h->d_hvec, (size_t)8 * kLMax);
+    al.get(&h->d_vh, (size_t)h->mc);
+    al.get(&h->d_vl, (size_t)h->mc);
     al.get(&h->d_upart, (size_t)h->coarse_blocks);
     al.get(&h->d_cscal, 8);
     al.get(&h->d_cint, 4);
@@ -469,10 +472,16 @@ id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64
   IDSK_CUDA(h, cudaMemcpyAsync(h->d_Jin, jh, sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->st));
   IDSK_CUDA(h, cudaMemcpyAsync(h->d_Pin, P, sizeof(double) * k * n, cudaMemcpyDefault, h->st));
   IDSK_CUDA(h, launch_recon_error(d_A, lda, h->m, n, h->cfg.dtype, h->d_Jin, h->d_Pin, k,
-                                  h->d_part, h->rec_blocks, h->d_out3, h->st));
+                                  h->d_part, h->rec_blocks, h->d_out3, h->d_status, h->st));
   double o[3];
+  int32_t dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(o, h->d_out3, sizeof(o), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(&dst, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
   IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (dst) {
+    h->poisoned = true;
+    return ID_ERR_TIMEOUT;
+  }
   if (rel_fro) *rel_fro = o[1] > 0.0 ? sqrt(o[0] / o[1]) : 0.0;
   if (rel_max) *rel_max = o[2];
   return ID_OK;

@@ -13,7 +13,14 @@
 // A downdated norm that lost more than 20 bits to cancellation is recomputed
 // from its definition ||A^(s+1)(s+1:, j)||^2.  The pivot rule is the largest
 // residual norm, ties to the lowest index; pivoting stops below the rank
-// tolerance.  Everything is FP64; reductions run in a fixed order.
+// tolerance.  Reductions run in a fixed order.
+//
+// Precision: FP64 throughout, except the one O(m_c n) product per step,
+// A_c^T v_s.  For FP32 data it runs on the FP32 units as exact FP32
+// products of A_c with v_s split into an FP32 pair, summed as FP32 pairs
+// (about 48 significant bits): FP64 arithmetic on this GPU is too slow for a
+// pass over A_c at memory speed, while the FP32 units are not.  Each CTA owns
+// whole columns, so no cross-CTA partial sums are needed.
 #include <float.h>
 
 #include <algorithm>
@@ -170,11 +177,13 @@ __global__ void pivcol_kernel(const T* __restrict__ Ac, int64_t mc, int s,
 __global__ void house_kernel(int s, int nblk, double* __restrict__ V, int64_t mc,
                              const double* __restrict__ upart, double* __restrict__ Rc, int n,
                              double* __restrict__ cscal, const int* __restrict__ cint) {
-  if (cint[CI_STOP] || threadIdx.x != 0) return;
+  if (cint[CI_STOP]) return;
+  double part = 0.0;   // fixed order: lane-strided partial sums, then shuffles
+  for (int b = threadIdx.x; b < nblk; b += 32) part += upart[b];
+  const double sigma = warp_sum(part);
+  if (threadIdx.x != 0) return;
   const int p = cint[CI_P];
   const double alpha = V[(int64_t)s * mc + s];
-  double sigma = 0.0;
-  for (int b = 0; b < nblk; ++b) sigma += upart[b];
   double beta = alpha, tau = 0.0, den = 0.0;
   if (sigma != 0.0) {
     const double nrm = sqrt(alpha * alpha + sigma);
@@ -191,25 +200,16 @@ __global__ void house_kernel(int s, int nblk, double* __restrict__ V, int64_t mc
   Rc[(int64_t)s * n + p] = beta;
 }
 
-// v_s = u / (alpha - beta) (rows > s), then per-block partials of A^T v_s
-// (non-pivoted columns) and V_s^T v_s.
-template <typename T>
-__global__ void __launch_bounds__(256) gemv_kernel(const T* __restrict__ Ac, int64_t mc, int n,
-                                                   int s, double* __restrict__ V,
-                                                   const int* __restrict__ colpos,
-                                                   double* __restrict__ gpart, int64_t ldg,
-                                                   int64_t hoff, int rows_per_block,
-                                                   const double* __restrict__ cscal,
-                                                   const int* __restrict__ cint) {
-  extern __shared__ double vsh[];   // rows_per_block
+// v_s = u / (alpha - beta) on rows > s (written back into V), v_s[s] = 1, and
+// its FP32 pair (hi, lo) for the double-float GEMV below.
+__global__ void scale_kernel(int64_t mc, int s, double* __restrict__ V, float* __restrict__ vh,
+                             float* __restrict__ vl, const double* __restrict__ cscal,
+                             const int* __restrict__ cint) {
   if (cint[CI_STOP]) return;
   const double den = cscal[CS_DEN];
   const double sigma = cscal[CS_SIGMA];
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t r1 = (mc < r0 + rows_per_block) ? mc : r0 + rows_per_block;
-  const int nr = (int)(r1 - r0);
-  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-    const int64_t i = r0 + q;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mc;
+       i += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     if (i == s) {
       v = 1.0;
@@ -217,44 +217,129 @@ __global__ void __launch_bounds__(256) gemv_kernel(const T* __restrict__ Ac, int
       v = sigma != 0.0 ? V[(int64_t)s * mc + i] / den : 0.0;
       V[(int64_t)s * mc + i] = v;
     }
-    vsh[q] = v;
+    const float hi = (float)v;
+    vh[i] = hi;
+    vl[i] = (float)(v - (double)hi);
+  }
+}
+
+// a * (bh + bl) added to the FP32 pair (hi, lo): exact product error by FMA,
+// TwoSum for the running sum, small terms gathered in lo (about 48 bits).
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float bh, float bl) {
+  const float p = a * bh;
+  const float pe = fmaf(a, bh, -p);
+  const float q = fmaf(a, bl, pe);
+  const float t = hi + p;
+  const float bp = t - hi;
+  const float err = (hi - (t - bp)) + (p - bp);
+  hi = t;
+  lo += err + q;
+}
+
+// Partial g_j = A(rows, j)^T v_s for groups of 8 columns and one of RS row
+// ranges per CTA (partials gpart[rs][j], summed in a fixed order by
+// finalize), and partial h_t = V(rows, t)^T v_s for t < s in the CTAs after
+// the column groups.  FP32 data: FP32 products summed as FP32 pairs; FP64
+// data and the h terms: FP64.  The row loop is unrolled by 4 so that 32
+// loads are in flight per thread.
+constexpr int GCOLS = 8;
+constexpr int RS = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_cols_kernel(
+    const T* __restrict__ Ac, int64_t mc, int n, int s, const double* __restrict__ V,
+    const float* __restrict__ vh, const float* __restrict__ vl, int ngroups,
+    double* __restrict__ gpart, double* __restrict__ hpart, const int* __restrict__ cint) {
+  __shared__ double sh[GCOLS][8];
+  if (cint[CI_STOP]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t span = mc - s;
+  const int64_t chunk = (span + RS - 1) / RS;
+  if ((int)blockIdx.x >= ngroups * RS) {   // partial h_t
+    const int b = blockIdx.x - ngroups * RS;
+    const int t = b / RS, rs = b - t * RS;
+    const int64_t i0 = s + rs * chunk, i1 = min(mc, i0 + chunk);
+    double acc = 0.0;
+    const double* col = V + (int64_t)t * mc;
+    for (int64_t i = i0 + tid; i < i1; i += 256) acc += col[i] * ((double)vh[i] + (double)vl[i]);
+    acc = warp_sum(acc);
+    if (lane == 0) sh[0][warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double r = 0.0;
+      for (int w = 0; w < 8; ++w) r += sh[0][w];
+      hpart[rs * kLMax + t] = r;
+    }
+    return;
+  }
+  const int grp = blockIdx.x / RS, rs = blockIdx.x - grp * RS;
+  const int64_t i0 = s + rs * chunk, i1 = min(mc, i0 + chunk);
+  const int j0 = grp * GCOLS;
+  const T* cols[GCOLS];
+#pragma unroll
+  for (int q = 0; q < GCOLS; ++q) cols[q] = Ac + (int64_t)min(j0 + q, n - 1) * mc;
+  double r[GCOLS];
+  if (sizeof(T) == 4) {
+    float hi[GCOLS], lo[GCOLS];
+#pragma unroll
+    for (int q = 0; q < GCOLS; ++q) hi[q] = lo[q] = 0.f;
+    int64_t i = i0 + tid;
+    for (; i + 3 * 256 < i1; i += 4 * 256) {
+      float a[4][GCOLS], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        bh[u] = vh[i + u * 256];
+        bl[u] = vl[i + u * 256];
+#pragma unroll
+        for (int q = 0; q < GCOLS; ++q) a[u][q] = (float)cols[q][i + u * 256];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < GCOLS; ++q) df_acc(hi[q], lo[q], a[u][q], bh[u], bl[u]);
+    }
+    for (; i < i1; i += 256) {
+      const float bh = vh[i], bl = vl[i];
+#pragma unroll
+      for (int q = 0; q < GCOLS; ++q) df_acc(hi[q], lo[q], (float)cols[q][i], bh, bl);
+    }
+#pragma unroll
+    for (int q = 0; q < GCOLS; ++q) r[q] = (double)hi[q] + (double)lo[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < GCOLS; ++q) r[q] = 0.0;
+    for (int64_t i = i0 + tid; i < i1; i += 256) {
+      const double b = (double)vh[i] + (double)vl[i];
+#pragma unroll
+      for (int q = 0; q < GCOLS; ++q) r[q] += (double)cols[q][i] * b;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < GCOLS; ++q) {
+    const double v = warp_sum(r[q]);
+    if (lane == 0) sh[q][warp] = v;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* gp = gpart + (int64_t)blockIdx.x * ldg;
-  // h_t = V(:, t)^T v_s, t < s
-  for (int t = warp; t < s; t += nw) {
-    const double* col = V + (int64_t)t * mc + r0;
+  if (tid < GCOLS && j0 + tid < n) {
     double acc = 0.0;
-    for (int q = lane; q < nr; q += 32) acc += col[q] * vsh[q];
-    acc = warp_sum(acc);
-    if (lane == 0) gp[hoff + t] = acc;
-  }
-  // g_j = A(:, j)^T v_s for non-pivoted j
-  for (int j = warp; j < n; j += nw) {
-    if (colpos[j] >= 0) continue;
-    const T* col = Ac + (int64_t)j * mc + r0;
-    double acc = 0.0;
-    for (int q = lane; q < nr; q += 32) acc += (double)col[q] * vsh[q];
-    acc = warp_sum(acc);
-    if (lane == 0) gp[j] = acc;
+    for (int w = 0; w < 8; ++w) acc += sh[tid][w];
+    gpart[(int64_t)rs * n + j0 + tid] = acc;
   }
 }
 
 template <typename T>
 __global__ void finalize_kernel(const T* __restrict__ Ac, int64_t mc, int n, int s,
                                 const double* __restrict__ V, double* __restrict__ F, int64_t ldf,
-                                const double* __restrict__ gpart, int64_t ldg, int64_t hoff,
-                                int nblk, const int* __restrict__ colpos,
-                                double* __restrict__ Rc, double* __restrict__ nu2,
-                                const double* __restrict__ nu20, int* __restrict__ rlist,
-                                const double* __restrict__ cscal, int* __restrict__ cint) {
+                                const double* __restrict__ gpart, const double* __restrict__ hpart,
+                                const int* __restrict__ colpos, double* __restrict__ Rc,
+                                double* __restrict__ nu2, const double* __restrict__ nu20,
+                                int* __restrict__ rlist, const double* __restrict__ cscal,
+                                int* __restrict__ cint) {
   __shared__ double h[kLMax];
   __shared__ double vrow[kLMax + 1];
   if (cint[CI_STOP]) return;
   for (int t = threadIdx.x; t < s; t += blockDim.x) {
     double acc = 0.0;
-    for (int b = 0; b < nblk; ++b) acc += gpart[(int64_t)b * ldg + hoff + t];
+    for (int rs = 0; rs < RS; ++rs) acc += hpart[rs * kLMax + t];
     h[t] = acc;
   }
   for (int t = threadIdx.x; t <= s; t += blockDim.x) vrow[t] = V[(int64_t)t * mc + s];
@@ -267,11 +352,11 @@ __global__ void finalize_kernel(const T* __restrict__ Ac, int64_t mc, int n, int
     return;
   }
   const double tau = cscal[CS_TAU];
-  double g = 0.0;
-  for (int b = 0; b < nblk; ++b) g += gpart[(int64_t)b * ldg + j];
   double fh = 0.0;
   for (int t = 0; t < s; ++t) fh += F[(int64_t)t * ldf + j] * h[t];
-  const double fjs = tau * (g - fh);
+  double gj = 0.0;
+  for (int rs = 0; rs < RS; ++rs) gj += gpart[(int64_t)rs * n + j];
+  const double fjs = tau * (gj - fh);
   F[(int64_t)s * ldf + j] = fjs;
   double r = (double)Ac[s + (int64_t)j * mc];
   for (int t = 0; t < s; ++t) r -= vrow[t] * F[(int64_t)t * ldf + j];
@@ -329,8 +414,7 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   const int k = h->k;
   const int kmax = (int)std::min<int64_t>(k, std::min<int64_t>(mc, n64));
   const int64_t ldf = h->n_max;
-  const int64_t ldg = h->n_max + kLMax;
-  const int64_t hoff = h->n_max;
+  const int ngroups = (n + GCOLS - 1) / GCOLS;
   int rpb = (int)((mc + 2 * h->nsm - 1) / (2 * h->nsm));
   rpb = std::max(32, ((rpb + 31) / 32) * 32);
   rpb = std::min(rpb, 4096);
@@ -348,15 +432,17 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
                                            h->d_cint);
     house_kernel<<<1, 32, 0, st>>>(s, nblk, h->d_V, mc, h->d_upart, h->d_Rc, n, h->d_cscal,
                                    h->d_cint);
-    gemv_kernel<T><<<nblk, 256, sizeof(double) * rpb, st>>>(Ac, mc, n, s, h->d_V, h->d_colposc,
-                                                            h->d_gpart, ldg, hoff, rpb,
-                                                            h->d_cscal, h->d_cint);
+    scale_kernel<<<2 * h->nsm, 256, 0, st>>>(mc, s, h->d_V, h->d_vh, h->d_vl, h->d_cscal,
+                                             h->d_cint);
+    gemv_cols_kernel<T><<<(ngroups + s) * RS, 256, 0, st>>>(Ac, mc, n, s, h->d_V, h->d_vh,
+                                                            h->d_vl, ngroups, h->d_gvec,
+                                                            h->d_hvec, h->d_cint);
     finalize_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(
-        Ac, mc, n, s, h->d_V, h->d_F, ldf, h->d_gpart, ldg, hoff, nblk, h->d_colposc, h->d_Rc,
+        Ac, mc, n, s, h->d_V, h->d_F, ldf, h->d_gvec, h->d_hvec, h->d_colposc, h->d_Rc,
         h->d_nu2, h->d_nu20, h->d_rlist, h->d_cscal, h->d_cint);
     recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, s, h->d_V, h->d_F, ldf, h->d_rlist, h->d_nu2,
                                             h->d_nu20, h->d_cint);
-    count_launches(6);
+    count_launches(7);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -148,7 +148,10 @@ struct id_sketch {
   double* d_F = nullptr;      // n_max x k
   double* d_nu2 = nullptr;    // n_max
   double* d_nu20 = nullptr;   // n_max
-  double* d_gpart = nullptr;  // coarse_blocks x (n_max + k)
+  double* d_gvec = nullptr;   // n_max: A_c^T v_s
+  double* d_hvec = nullptr;   // kLMax: V_s^T v_s
+  float* d_vh = nullptr;      // mc: v_s as an FP32 pair (hi)
+  float* d_vl = nullptr;      // mc: (lo)
   double* d_upart = nullptr;  // coarse_blocks
   double* d_cscal = nullptr;  // 8 scalars
   int* d_cint = nullptr;      // 4 ints: pivot, stop, nrecompute, k_out
@@ -183,7 +186,11 @@ cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, con
 cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
-                               double* out3, cudaStream_t st);
+                               double* out3, int* status, cudaStream_t st);
+int recon_tc_grid(int64_t m, int64_t n, int nsm);
+cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
+                            const double* P, int k, double* part, int grid, int* status,
+                            cudaStream_t st);
 void gaussian_table_host(float* vals, uint16_t* bits);
 void count_launches(int64_t n);
 }  // namespace idsk

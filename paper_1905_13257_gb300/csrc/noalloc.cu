@@ -18,8 +18,9 @@
 // cudaGetSymbolAddress and keeps it.  That first call should come before any
 // stream capture.  All calls on a device share the array, and it keeps the
 // last call's contents.  Nothing in it needs clearing: every slot a call
-// reads was written earlier in the same call.  Calls that overlap on the GPU
-// (e.g. on two streams) race on the array.
+// reads was written earlier in the same call, and the one word that must start
+// at zero (the timeout flag) is cleared at the start of every call.  Calls
+// that overlap on the GPU (e.g. on two streams) race on the array.
 #include <math.h>
 
 #include <algorithm>
@@ -31,7 +32,7 @@ namespace {
 
 constexpr int kMaxBlocks = 2048;                      // partial-sum slots
 constexpr size_t kPartOff = 0;                        // 3 doubles per CTA
-constexpr size_t kOutOff = 3 * (size_t)kMaxBlocks;    // 3 result scalars (+1 pad)
+constexpr size_t kOutOff = 3 * (size_t)kMaxBlocks;    // 3 result scalars, then the status word
 constexpr size_t kJOff = kOutOff + 4;                 // kRecKMax int32 = 32 doubles
 constexpr size_t kPOff = kJOff + idsk::kRecKMax / 2;  // P, up to ID_NOALLOC_MAX_KN
 constexpr size_t kTotal = kPOff + (size_t)ID_NOALLOC_MAX_KN;
@@ -88,13 +89,18 @@ extern "C" id_status id_reconstruct_error_noalloc(const void* d_A, int64_t lda, 
       cudaMemcpyAsync(dP, P, sizeof(double) * k * n, cudaMemcpyDefault, st) != cudaSuccess)
     return ID_ERR_CUDA;
   const int nblk = std::min(8 * nsm, kMaxBlocks);
+  int* dstatus = reinterpret_cast<int*>(base + kOutOff + 3);   // cleared for this call
+  if (cudaMemsetAsync(dstatus, 0, sizeof(int), st) != cudaSuccess) return ID_ERR_CUDA;
   if (idsk::launch_recon_error(d_A, lda, m, n, dtype, dJ, dP, k, base + kPartOff, nblk,
-                               base + kOutOff, st) != cudaSuccess)
+                               base + kOutOff, dstatus, st) != cudaSuccess)
     return ID_ERR_CUDA;
   double o[3];
+  int flag = 0;
   if (cudaMemcpyAsync(o, base + kOutOff, sizeof(o), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&flag, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return ID_ERR_CUDA;
+  if (flag) return ID_ERR_TIMEOUT;
   if (rel_fro) *rel_fro = o[1] > 0.0 ? sqrt(o[0] / o[1]) : 0.0;
   if (rel_max) *rel_max = o[2];
   return ID_OK;

@@ -1,0 +1,355 @@
+// Fused reconstruction-error pass on the tcgen05 tensor cores (FP32 data).
+//
+// One read of A gives ||A - A(:,J) P||_F^2, ||A||_F^2 and
+// max |A_ij - A_hat_ij| / |A_ij| over A_ij != 0 (the Frobenius metric of
+// Sec. 3.3 and the entry-wise metric of Sec. 3.1), A_hat = A(:,J) P being the
+// ID of eq. eqn:id written for columns.
+//
+// Each CTA owns one 256-column tile C and a contiguous range of 128-row
+// blocks R (the CTAs of one row range run side by side, so the skeleton rows
+// A(R, J) they all gather come from L2 after the first read):
+//   A_hat(R, C) = A(R, J) P(:, C)   M = 128 rows, N = 256 columns, K = k <= 64
+// Precision: A(R, J) (FP32) and P (FP64) are each split into three bfloat16
+// pieces and the six products with an exponent sum up to 2^-16 are formed
+// (a0p0, a0p1, a1p0, a0p2, a1p1, a2p0), which reproduces A_hat to about FP32
+// accuracy; the residual and its square are then taken in FP32 against A
+// itself, read once from global memory by the epilogue.
+//
+// Warp roles:
+//   warps 0-7   epilogue: stream A(R, C) (warp w: TMEM lane quarter w % 4,
+//               128 columns w / 4), read A_hat from TMEM, accumulate the
+//               statistics
+//   warps 8-11  gather A(R, J): one row per thread, all k loads of the row
+//               issued at once, split, store the pieces (double-buffered)
+//   warp 12     TMEM allocation and the single-thread tcgen05.mma issue
+// 13 warps keep at most 4 warps per SM sub-partition (128 registers each).
+// Waits are bounded as in the sketch kernel; on timeout the status word is
+// set and the host reports ID_ERR_TIMEOUT.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "idsk_internal.h"
+#include "tc_common.cuh"
+
+namespace idsk {
+namespace {
+
+using namespace tc;
+
+constexpr int TR = 128;
+constexpr int TN = 256;                  // columns per CTA tile
+constexpr int KP = 64;                   // padded rank
+constexpr int NEPI = 8;
+constexpr int NGAT = 4;
+constexpr int MMA_WARP = NEPI + NGAT;    // 12
+constexpr int NTHREADS = (NEPI + NGAT + 1) * 32;
+constexpr uint32_t S_PIECE = TR * KP * 2;   // 16 KB
+constexpr uint32_t P_PIECE = TN * KP * 2;   // 32 KB
+constexpr uint32_t IDESC = idesc_bf16(TR, TN, 0);
+
+enum { B_SF0 = 0, B_SF1, B_SE0, B_SE1, B_DF0, B_DF1, B_DE0, B_DE1, B_DONE, NBAR };
+
+// Optional timeline of CTA 0, compiled only when IDSK_RC_TRACE is defined by a
+// profiling harness.
+#ifdef IDSK_RC_TRACE
+__device__ long long g_rc_trace[4][4096];
+#define RC_TRACE(role, idx)                                                   \
+  do {                                                                        \
+    if (blockIdx.x == 0 && (idx) < 4096) g_rc_trace[role][idx] = clock64();   \
+  } while (0)
+#else
+#define RC_TRACE(role, idx) \
+  do {                      \
+  } while (0)
+#endif
+
+// piece products: (A piece, P piece)
+__constant__ int kCombA[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int kCombP[6] = {0, 1, 0, 2, 1, 0};
+
+template <typename T>
+struct Kahan {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+__device__ __forceinline__ void split3(float x, uint16_t& p0, uint16_t& p1, uint16_t& p2) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
+  p0 = *reinterpret_cast<const uint16_t*>(&h0);
+  p1 = *reinterpret_cast<const uint16_t*>(&h1);
+  p2 = *reinterpret_cast<const uint16_t*>(&h2);
+}
+
+__device__ __forceinline__ void split3(double x, uint16_t& p0, uint16_t& p1, uint16_t& p2) {
+  const __nv_bfloat16 h0 = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(h0);
+  const __nv_bfloat16 h1 = __double2bfloat16(r1);
+  const double r2 = r1 - (double)__bfloat162float(h1);
+  const __nv_bfloat16 h2 = __double2bfloat16(r2);
+  p0 = *reinterpret_cast<const uint16_t*>(&h0);
+  p1 = *reinterpret_cast<const uint16_t*>(&h1);
+  p2 = *reinterpret_cast<const uint16_t*>(&h2);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    recon_tc_kernel(const float* __restrict__ A, int64_t lda, int64_t m, int n,
+                    const int* __restrict__ J, const double* __restrict__ P, int k,
+                    double* __restrict__ part, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t s_p = base;                       // P pieces: 3 x 32 KB
+  const uint32_t s_s = s_p + 3u * P_PIECE;         // S pieces: 2 buffers x 3 x 16 KB
+  const uint32_t bars = s_s + 2u * 3u * S_PIECE;
+  const uint32_t tmem_slot = bars + NBAR * 8u;
+  const uint32_t abort_flag = tmem_slot + 4u;
+  __shared__ int Js[kRecKMax];
+  __shared__ double red[3][NEPI];
+  auto bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n_ct = (n + TN - 1) / TN;
+  const int ct = blockIdx.x % n_ct;
+  const int rr = blockIdx.x / n_ct;
+  const int nrr = gridDim.x / n_ct;
+  const int64_t nrb = (m + TR - 1) / TR;
+  const int64_t rb_begin = nrb * rr / nrr, rb_end = nrb * (rr + 1) / nrr;
+  const int nloc = (int)(rb_end - rb_begin);
+  const int c0 = ct * TN;
+
+  if (tid == 0) {
+    mbar_init(bar(B_SF0), NGAT);
+    mbar_init(bar(B_SF1), NGAT);
+    mbar_init(bar(B_SE0), 1);
+    mbar_init(bar(B_SE1), 1);
+    mbar_init(bar(B_DF0), 1);
+    mbar_init(bar(B_DF1), 1);
+    mbar_init(bar(B_DE0), NEPI);
+    mbar_init(bar(B_DE1), NEPI);
+    mbar_init(bar(B_DONE), 1);
+    st_volatile_shared(abort_flag, 0);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int u = tid; u < k; u += NTHREADS) Js[u] = J[u];
+  // P(:, C) split into three bf16 pieces: K-major B operand, row = column c
+  for (int e = tid; e < TN * KP; e += NTHREADS) {
+    const int c = e / KP, t = e % KP;
+    double v = 0.0;
+    if (t < k && c0 + c < n) v = P[(int64_t)t * n + c0 + c];
+    uint16_t p0, p1, p2;
+    split3(v, p0, p1, p2);
+    const uint32_t off = swz((uint32_t)c, (uint32_t)t, 1024u);
+    st_shared_u16(s_p + off, p0);
+    st_shared_u16(s_p + P_PIECE + off, p1);
+    st_shared_u16(s_p + 2u * P_PIECE + off, p2);
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     tmem_slot)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(tmem_slot) : "memory");
+
+  if (warp < NEPI) {
+    // -------------------------------------------------------------- epilogue
+    const int q = warp & 3;                  // TMEM lane quarter
+    const int ch = warp >> 2;                // column half of the tile (128 columns)
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    Kahan<float> res, tot;
+    float mx = 0.f;
+    // per row block: four chunks of 32 columns; the 32 loads of a chunk are
+    // issued before its TMEM read.
+    // Per element: one residual, two FMAs into chunk sums (folded into the
+    // Kahan accumulators once per chunk), and a division-free running maximum
+    // of |e| / |a| kept as the pair (bn, bd) = (|e|, |a|) of the best entry.
+    float bn = 0.f, bd = 1.f;
+    bool ok = true;
+    for (int i = 0; i < nloc && ok; ++i) {
+      const int b = i & 1;
+      const int64_t r = (rb_begin + i) * TR + q * 32 + lane;
+      const bool rok = r < m;
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const int cb = c0 + ch * 128 + c4 * 32;
+        const bool full = rok && (cb + 31 < n);
+        float v[32];
+        if (full) {
+          const float* p = A + r + (int64_t)cb * lda;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __ldcs(p + (int64_t)j * lda);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            v[j] = (rok && cb + j < n) ? __ldcs(A + r + (int64_t)(cb + j) * lda) : 0.f;
+        }
+        if (c4 == 0) {
+          if (!mbar_wait(bar(B_DF0 + b), (i >> 1) & 1, abort_flag, 128)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        float d[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(b * TN + ch * 128 + c4 * 32), d);
+        if (!full) {   // entries outside the matrix contribute nothing
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (!(rok && cb + j < n)) d[j] = 0.f;
+        }
+        float se = 0.f, sa = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float a = v[j];
+          const float e = a - d[j];
+          se = fmaf(e, e, se);
+          sa = fmaf(a, a, sa);
+          const float ae = fabsf(e), aa = fabsf(a);
+          const bool better = (aa != 0.f) && (ae * bd > bn * aa);
+          bn = better ? ae : bn;
+          bd = better ? aa : bd;
+        }
+        res.add(se);
+        tot.add(sa);
+      }
+      if (!ok) break;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_DE0 + b));
+      if (warp == 0 && lane == 0) RC_TRACE(0, i);
+    }
+    mx = bn / bd;
+    double s0 = (double)res.s - (double)res.c, s1 = (double)tot.s - (double)tot.c, s2 = mx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 = fmax(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+    }
+    if (lane == 0) {
+      red[0][warp] = s0;
+      red[1][warp] = s1;
+      red[2][warp] = s2;
+    }
+  } else if (warp < MMA_WARP) {
+    // ---------------------------------------------------------------- gather
+    const int rl = tid - NEPI * 32;          // row of the block owned by this thread
+    uint8_t* sm_gen = smem_raw + (s_s - smem_u32(smem_raw));
+    for (int i = 0; i < nloc; ++i) {
+      const int b = i & 1;
+      const int64_t r = (rb_begin + i) * TR + rl;
+      const bool rok = r < m;
+      float x[KP];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) x[t] = (t < k && rok) ? A[r + (int64_t)Js[t] * lda] : 0.f;
+      if (i >= 2 && !mbar_wait(bar(B_SE0 + b), ((i >> 1) - 1) & 1, abort_flag, 64)) break;
+      uint8_t* sbp = sm_gen + (size_t)b * 3u * S_PIECE;
+#pragma unroll
+      for (int t0 = 0; t0 < KP; t0 += 8) {
+        uint32_t w[3][4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          uint16_t a0, a1, a2, b0, b1, b2;
+          split3(x[t0 + u], a0, a1, a2);
+          split3(x[t0 + u + 1], b0, b1, b2);
+          w[0][u >> 1] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+          w[1][u >> 1] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+          w[2][u >> 1] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+        }
+        const uint32_t off = swz((uint32_t)rl, (uint32_t)t0, 1024u);   // 16 bytes
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+          *reinterpret_cast<uint4*>(sbp + p * S_PIECE + off) =
+              make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_SF0 + b));
+      if (rl == 0) RC_TRACE(1, i);
+    }
+  } else if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    for (int i = 0; i < nloc; ++i) {
+      const int b = i & 1;
+      if (!mbar_wait(bar(B_SF0 + b), (i >> 1) & 1, abort_flag, 64)) break;
+      if (i >= 2 && !mbar_wait(bar(B_DE0 + b), ((i >> 1) - 1) & 1, abort_flag, 64)) break;
+      tc_fence_after();
+      RC_TRACE(2, i);
+      const uint32_t sb = s_s + (uint32_t)b * 3u * S_PIECE;
+      const uint32_t d = tmem + (uint32_t)(b * TN);
+      for (int kk = 0; kk < KP / 16; ++kk) {
+#pragma unroll
+        for (int cmb = 0; cmb < 6; ++cmb) {
+          const uint32_t ko = (uint32_t)kk * 32u;
+          mma_bf16(d, sdesc(sb + (uint32_t)kCombA[cmb] * S_PIECE + ko, 0u, 1024u),
+                   sdesc(s_p + (uint32_t)kCombP[cmb] * P_PIECE + ko, 0u, 1024u), IDESC,
+                   (uint32_t)(kk | cmb));
+        }
+      }
+      mma_commit(bar(B_DF0 + b));
+      mma_commit(bar(B_SE0 + b));
+    }
+    mma_commit(bar(B_DONE));
+    const long long t0 = clock64();
+    while (!mbar_try(bar(B_DONE), 0)) {
+      if (clock64() - t0 > kWaitCycles) {
+        st_volatile_shared(abort_flag, 1);
+        break;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+  if (tid == 0) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int w = 0; w < NEPI; ++w) {
+      a0 += red[0][w];
+      a1 += red[1][w];
+      a2 = fmax(a2, red[2][w]);
+    }
+    part[3 * blockIdx.x + 0] = a0;
+    part[3 * blockIdx.x + 1] = a1;
+    part[3 * blockIdx.x + 2] = a2;
+    if (ld_volatile_shared(abort_flag)) atomicOr(status, 1);
+  }
+}
+
+}  // namespace
+
+int recon_tc_grid(int64_t m, int64_t n, int nsm) {
+  const int n_ct = (int)((n + TN - 1) / TN);
+  const int64_t nrb = (m + TR - 1) / TR;
+  const int rr = (int)std::max<int64_t>(1, std::min<int64_t>(nrb, nsm / std::max(1, n_ct)));
+  return n_ct * rr;
+}
+
+cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
+                            const double* P, int k, double* part, int grid, int* status,
+                            cudaStream_t st) {
+  const size_t sm = 1024 + 3u * P_PIECE + 6u * S_PIECE + NBAR * 8 + 16;
+  cudaError_t e = cudaFuncSetAttribute(recon_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  recon_tc_kernel<<<grid, NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace idsk

@@ -39,9 +39,12 @@
 #include <algorithm>
 
 #include "idsk_internal.h"
+#include "tc_common.cuh"
 
 namespace idsk {
 namespace {
+
+using namespace tc;
 
 constexpr int TR = 128;                 // rows per tile
 constexpr int TCOLS = 128;              // columns per tile
@@ -54,8 +57,9 @@ constexpr uint32_t PIECE_BYTES = TR * TCOLS * 2;     // 32 KB
 constexpr uint32_t PSI_BYTES = LP * TR * 2;          // 16 KB
 constexpr uint32_t OMEGA_TILE_BYTES = LP * TCOLS * 2;  // 16 KB
 constexpr int TMEM_COLS = 512;
+constexpr uint32_t IDESC_W = tc::idesc_bf16(128, LP, 0);   // A^T K-major (K = rows)
+constexpr uint32_t IDESC_Y = tc::idesc_bf16(128, LP, 1);   // A MN-major (M = rows)
 constexpr int TMEM_Y = kTcMaxTiles * LP;             // Y accumulators after W^T
-constexpr long long kWaitCycles = 4000000000LL;      // ~2 s: a wait this long is a bug
 
 // Optional timeline of CTA 0 (clock64 stamps per role), compiled only when
 // IDSK_TC_TRACE is defined by a profiling harness.
@@ -83,149 +87,6 @@ struct Smem {
   uint32_t tmem_slot;
   uint32_t abort_flag;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ int ld_volatile_shared(uint32_t a) {
-  int v;
-  asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_volatile_shared(uint32_t a, int v) {
-  asm volatile("st.volatile.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
-// Bounded wait on a phase of an mbarrier; false (and the abort flag raised) on
-// timeout or when another role already aborted.  Between polls the thread
-// sleeps (sleep_ns), so that waiting roles leave the issue slots to the
-// converter warps that share their schedulers.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag,
-                          uint32_t sleep_ns = 64) {
-  if (mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  for (uint32_t it = 0;; ++it) {
-    __nanosleep(sleep_ns);
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 7) == 7) {
-      if (ld_volatile_shared(abort_flag)) return false;
-      if (clock64() - t0 > kWaitCycles) {
-        st_volatile_shared(abort_flag, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: start address, leading / stride byte
-// offsets, descriptor version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-constexpr uint32_t IDESC_W = idesc_bf16(128, LP, 0);   // A^T K-major (K = rows)
-constexpr uint32_t IDESC_Y = idesc_bf16(128, LP, 1);   // A MN-major (M = rows)
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// Byte offset of element (mn, k) in a K-major 128B-swizzled operand whose
-// 8-row groups are `sbo` bytes apart and whose two 64-wide K halves are 1 KB
-// apart (tile of up to 128 x 128 bf16, atoms (mn/8, k/64) at (mn/8)*sbo +
-// (k/64)*1024).
-__device__ __forceinline__ uint32_t swz(uint32_t mn, uint32_t k, uint32_t sbo) {
-  return (mn >> 3) * sbo + (k >> 6) * 1024u + (mn & 7u) * 128u +
-         ((((k & 63u) >> 3) ^ (mn & 7u)) << 4) + (k & 7u) * 2u;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-__device__ __forceinline__ void st_shared_v2(uint32_t a, uint32_t x, uint32_t y) {
-  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(x), "r"(y) : "memory");
-}
-
-__device__ __forceinline__ void st_shared_u16(uint32_t a, uint16_t v) {
-  asm volatile("st.shared.b16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
-}
-
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  __nv_bfloat16 h = __float2bfloat16_rn(x);
-  return *reinterpret_cast<uint16_t*>(&h);
-}
 
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
   const int64_t i = r % g.nx;
