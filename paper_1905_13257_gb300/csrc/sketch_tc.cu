@@ -34,7 +34,10 @@
 // Every mbarrier wait is bounded: on timeout the CTA raises an abort flag,
 // every role leaves its loop, in-flight MMAs are waited for (bounded) and the
 // TMEM is freed; the host reads the status word and reports ID_ERR_TIMEOUT.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -52,6 +55,10 @@ constexpr int NCONV = 8;                // converter warps
 constexpr int NEPI = 4;                 // epilogue warps
 constexpr int MMA_WARP = NCONV + NEPI;  // 12
 constexpr int NTHREADS = (NCONV + NEPI + 1) * 32;
+constexpr int PROD_WARP = MMA_WARP + 1;   // TMA producer (TMA form only)
+constexpr int NTHREADS_TMA = NTHREADS + 32;
+constexpr int NST = 4;                    // raw FP32 stages of 128 rows x 32 columns
+constexpr uint32_t RAW_BYTES = TR * 32 * 4;   // 16 KB
 constexpr int LP = 64;                  // padded sketch width: N of both products
 constexpr uint32_t PIECE_BYTES = TR * TCOLS * 2;     // 32 KB
 constexpr uint32_t PSI_BYTES = LP * TR * 2;          // 16 KB
@@ -77,16 +84,34 @@ __device__ long long g_tc_trace[4][8192];
 
 // barrier slots
 enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE1,
-       B_YF0, B_YF1, B_YE0, B_YE1, B_WF, B_WE, B_DONE, NBAR };
+       B_YF0, B_YF1, B_YE0, B_YE1, B_WF, B_WE, B_DONE, B_RF0, B_RE0 = B_RF0 + NST,
+       NBAR = B_RE0 + NST };
 
 struct Smem {
-  uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES]
+  uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES] (TMA form: one buffer)
+  uint32_t raw;      // TMA form: [NST][RAW_BYTES]
+  uint32_t rc;       // TMA form: coarse index of the 128 rows of the row block
   uint32_t omega;    // [kTcMaxTiles][OMEGA_TILE_BYTES]
   uint32_t psi;      // [2][PSI_BYTES]
   uint32_t bars;     // NBAR x 8 bytes
   uint32_t tmem_slot;
   uint32_t abort_flag;
 };
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// 2D tiled TMA load of one box (x = row, y = column) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
 
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
   const int64_t i = r % g.nx;
@@ -123,15 +148,19 @@ __device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window
   return y;
 }
 
-template <int NP>
-__global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Window w, int drain_blocks, int* __restrict__ status) {
+template <int NP, bool TMA>
+__global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
+    sketch_tc_kernel(SketchArgs a, Window w, int drain_blocks, int* __restrict__ status,
+                     const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   Smem S;
   S.pieces = base;
-  S.omega = S.pieces + 2u * NP * PIECE_BYTES;
+  S.omega = S.pieces + (TMA ? 1u : 2u) * NP * PIECE_BYTES;
   S.psi = S.omega + kTcMaxTiles * OMEGA_TILE_BYTES;
-  S.bars = S.psi + 2u * PSI_BYTES;
+  S.raw = S.psi + 2u * PSI_BYTES;
+  S.rc = S.raw + (TMA ? NST * RAW_BYTES : 0u);
+  S.bars = S.rc + (TMA ? TR * 8u : 0u);
   S.tmem_slot = S.bars + NBAR * 8u;
   S.abort_flag = S.tmem_slot + 4u;
   auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
@@ -160,11 +189,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
     mbar_init(bar(B_WF), 1);
     mbar_init(bar(B_WE), NEPI);
     mbar_init(bar(B_DONE), 1);
+    if (TMA) {
+      mbar_init(bar(B_FULL0), NCONV);   // one piece buffer: FULL0/FREE0 only
+      for (int st = 0; st < NST; ++st) {
+        mbar_init(bar(B_RF0 + st), 1);
+        mbar_init(bar(B_RE0 + st), NCONV);
+      }
+    }
     st_volatile_shared(S.abort_flag, 0);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // Omega(window, :) as a K-major bf16 B operand, resident for the kernel
-  for (int e = tid; e < kTcMaxTiles * TCOLS * LP; e += NTHREADS) {
+  constexpr int NT_ALL = TMA ? NTHREADS_TMA : NTHREADS;
+  for (int e = tid; e < kTcMaxTiles * TCOLS * LP; e += NT_ALL) {
     const int s = e % LP, c = e / LP;
     float v = 0.f;
     if (s < a.l && c < w.ncols) v = a.omega[(w.col_base + c) * a.l + s];
@@ -188,6 +225,74 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
   auto drain_due = [&](int i) { return ((i + 1) % drain_blocks) == 0 || i == nloc - 1; };
 
   if (warp < NCONV) {
+    if constexpr (TMA) {
+    // ------------------------------------------------------ converters (TMA)
+    // Raw FP32 boxes (32 columns x 128 rows, 512 B per column) arrive in an
+    // NST-stage ring; thread (warp w, lane l) splits column 4w + l/8, rows
+    // 4(l%8) + 32g of each box into the (single) piece buffer.
+    const int cl = warp * 4 + (lane >> 3);
+    const int rq = (lane & 7) * 4;
+    int64_t* rcs = reinterpret_cast<int64_t*>(smem_raw + (S.rc - smem_u32(smem_raw)));
+    const uint8_t* rawp = smem_raw + (S.raw - smem_u32(smem_raw));
+    int t = 0;
+    bool ok = true;
+    for (int i = 0; i < nloc && ok; ++i) {
+      const int64_t rbase = (rb_begin + i) * TR;
+      if (a.cg.on) {
+        asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
+        if (tid < TR) rcs[tid] = (rbase + tid < a.m) ? coarse_index_tc(rbase + tid, a.cg) : -1;
+        asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
+      }
+      for (int ct = 0; ct < nct && ok; ++ct, ++t) {
+        if (t >= 1 && !mbar_wait(bar(B_FREE0), (t - 1) & 1, S.abort_flag)) {
+          ok = false;
+          break;
+        }
+        for (int j = 0; j < 4; ++j) {
+          const int u = 4 * t + j, st = u % NST;
+          if (!mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) {
+            ok = false;
+            break;
+          }
+          const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
+          const int cc = 32 * j + cl;              // column inside the tile
+          const int wc = ct * TCOLS + cc;          // column inside the window
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int rr = 32 * g + rq;
+            const float4 x = *reinterpret_cast<const float4*>(raw + cl * TR + rr);
+            const uint32_t off = swz((uint32_t)cc, (uint32_t)rr, 2048u);
+            const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
+            st_shared_v2(S.pieces + off, h01, h23);
+            if (NP > 1) {
+              const float2 f01 =
+                  __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h01));
+              const float2 f23 =
+                  __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h23));
+              st_shared_v2(S.pieces + PIECE_BYTES + off, pack_bf16x2(x.x - f01.x, x.y - f01.y),
+                           pack_bf16x2(x.z - f23.x, x.w - f23.y));
+            }
+            if (a.cg.on && wc < w.ncols) {
+              float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc);
+              const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int q4 = 0; q4 < 4; ++q4) {
+                const int64_t rcv = rcs[rr + q4];
+                if (rcv >= 0) Ac[rcv] = xs[q4];
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_RE0 + st));
+        }
+        if (!ok) break;
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_FULL0));
+        if (warp == 0 && lane == 0) TC_TRACE(0, t);
+      }
+    }
+    } else {
     // ------------------------------------------------------------ converters
     // A tile is two half tiles of 64 columns; each thread owns 8 columns x 4
     // rows of a half tile.  The loads of the next half tile are issued before
@@ -264,6 +369,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
         if (lane == 0) mbar_arrive(bar(B_FULL0 + b));
         if (warp == 0 && lane == 0) TC_TRACE(0, t);
       }
+    }
     }
   } else if (warp < MMA_WARP) {
     // -------------------------------------------------------------- epilogue
@@ -363,7 +469,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
       }
       if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 2);
     }
-  } else if (lane == 0) {
+  } else if (warp == MMA_WARP && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     uint32_t accw = 0;   // bit ct: W^T accumulator of tile ct holds data
     int wd = 0;
@@ -377,8 +483,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
       const uint32_t psi_s = S.psi + (uint32_t)pb * PSI_BYTES;
       const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + pb * LP);
       for (int ct = 0; ct < nct; ++ct, ++t) {
-        const int b = t & 1;
-        if (!mbar_wait(bar(B_FULL0 + b), (t >> 1) & 1, S.abort_flag)) {
+        const int b = TMA ? 0 : (t & 1);
+        if (!mbar_wait(bar(B_FULL0 + b), TMA ? (t & 1) : ((t >> 1) & 1), S.abort_flag)) {
           ok = false;
           break;
         }
@@ -428,6 +534,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) sketch_tc_kernel(SketchArgs a, Wi
         break;
       }
     }
+  } else if (TMA && warp == PROD_WARP && lane == 0) {
+    // -------------------------------------------------------- TMA producer
+    const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
+    int u = 0;
+    bool ok = true;
+    for (int t = 0; t < ntile && ok; ++t) {
+      const int i = t / nct, ct = t - i * nct;
+      const int row = (int)((rb_begin + i) * TR);
+      for (int j = 0; j < 4; ++j, ++u) {
+        const int st = u % NST;
+        if (u >= NST && !mbar_wait(bar(B_RE0 + st), ((u / NST) - 1) & 1, S.abort_flag, 32)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(bar(B_RF0 + st), RAW_BYTES);
+        tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES, tm, row, ct * TCOLS + 32 * j,
+                    bar(B_RF0 + st));
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -456,10 +581,64 @@ __global__ void wpart_reduce_kernel(const double* __restrict__ wpart, int nslab,
   W[(int64_t)s * ldw + col_base + c] = acc;
 }
 
-template <int NP>
+template <int NP, bool TMA>
 size_t tc_smem_bytes() {
-  return 1024 + 2u * NP * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES + 2u * PSI_BYTES +
-         NBAR * 8 + 16;
+  return 1024 + (TMA ? 1u : 2u) * NP * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES +
+         2u * PSI_BYTES + (TMA ? NST * RAW_BYTES + TR * 8u : 0u) + NBAR * 8 + 16;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of the window's single segment: rows x columns FP32, boxes of
+// 128 rows x 32 columns, zero fill outside.  False when it cannot be built.
+bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
+  if (w.nseg != 1 || (((uintptr_t)w.seg[0].ptr) & 15u) != 0 || (w.seg[0].ld & 3) != 0)
+    return false;
+  const char* env = getenv("IDSKETCH_SKETCH_TMA");
+  if (env && env[0] == '0') return false;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)a.m, (cuuint64_t)w.seg[0].ncols};
+  const cuuint64_t strides[1] = {(cuuint64_t)w.seg[0].ld * 4u};
+  const cuuint32_t box[2] = {(cuuint32_t)TR, 32u};
+  const cuuint32_t es[2] = {1u, 1u};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(w.seg[0].ptr), dims,
+             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <int NP, bool TMA>
+cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int drain_blocks,
+                           int* status, const CUtensorMap& tm, cudaStream_t st) {
+  const size_t sm = tc_smem_bytes<NP, TMA>();
+  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  sketch_tc_kernel<NP, TMA><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(a, w, drain_blocks,
+                                                                              status, tm);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -470,21 +649,16 @@ cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, 
   if (w.ncols > kTcMaxTiles * TCOLS || a.l > LP) return cudaErrorInvalidValue;
   const int64_t nrb = (a.m + TR - 1) / TR;
   const int grid = (int)std::min<int64_t>(nrb, nsm);
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  const bool tma = make_tmap(a, w, &tm);
   cudaError_t e;
-  if (npieces == 1) {
-    const size_t sm = tc_smem_bytes<1>();
-    e = cudaFuncSetAttribute(sketch_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-    if (e != cudaSuccess) return e;
-    sketch_tc_kernel<1><<<grid, NTHREADS, sm, st>>>(a, w, drain_blocks, status);
-  } else {
-    const size_t sm = tc_smem_bytes<2>();
-    e = cudaFuncSetAttribute(sketch_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-    if (e != cudaSuccess) return e;
-    sketch_tc_kernel<2><<<grid, NTHREADS, sm, st>>>(a, w, drain_blocks, status);
-  }
-  e = cudaGetLastError();
+  if (npieces == 1)
+    e = tma ? launch_variant<1, true>(a, w, grid, drain_blocks, status, tm, st)
+            : launch_variant<1, false>(a, w, grid, drain_blocks, status, tm, st);
+  else
+    e = tma ? launch_variant<2, true>(a, w, grid, drain_blocks, status, tm, st)
+            : launch_variant<2, false>(a, w, grid, drain_blocks, status, tm, st);
   if (e != cudaSuccess) return e;
   const int tot = a.l * w.ncols;
   wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(a.wpart, grid, a.l, w.ncols, nrb, a.W,

@@ -297,3 +297,38 @@ def test_bf16_sketch_matches_oracle_on_rounded_data():
     assert rel(W.cpu().numpy(), Wo) <= 1e-5
     assert rel(Y.cpu().double().numpy(), Yo) <= 1e-5
     sk.close()
+
+
+@pytest.mark.parametrize("tma", ["1", "0"])
+def test_tensor_core_sketch_feeds(monkeypatch, tma):
+    """Both tensor-core feeds of A (TMA boxes for a single-segment window, and
+    register loads for a window made of several separate buffers) against
+    the oracle, with coarse gather and ragged m and n."""
+    monkeypatch.setenv("IDSKETCH_SKETCH_TMA", tma)
+    grid, nc, n, l = (20, 13, 12), 3, 300, 60
+    A = channel_field(grid, nc, n, seed=4, dtype=torch.float32, device=DEV)
+    m = A.shape[0]
+    assert m % 4 == 0
+    # separate, 16-byte aligned buffers: windows of several segments
+    parts = [A[:, j:j + 45].contiguous().T.contiguous().T for j in range(0, n, 45)]
+    sk = _sk(m=m, n_max=n, k=10, l=l, seed=6, dtype=torch.float32, grid=grid, ncomp=nc,
+             coarse_stride=(2, 3, 2), want_coarse=True, window_cols=256)
+    for p in parts:
+        sk.stream_columns(p)
+    W, Y, Ac = sk.sketches()
+    An = A.cpu().double().numpy()
+    Wo, Yo = oracle.sketch(An, oracle.psi(l, m, 6), oracle.omega(n, l, 6))
+    assert rel(W.cpu().numpy(), Wo) <= 1e-5
+    assert rel(Y.cpu().double().numpy(), Yo) <= 1e-5
+    rows = oracle.coarse_rows(grid, nc, (2, 3, 2))
+    assert np.array_equal(Ac.cpu().numpy(), A.cpu().numpy()[rows])
+    sk.close()
+    # one resident buffer: single-segment windows
+    sk = _sk(m=m, n_max=n, k=10, l=l, seed=6, dtype=torch.float32, grid=grid, ncomp=nc,
+             coarse_stride=(2, 3, 2), want_coarse=True, window_cols=n)
+    stream(sk, A, [32] * (n // 32) + [n % 32])
+    W2, Y2, Ac2 = sk.sketches()
+    assert rel(W2.cpu().numpy(), Wo) <= 1e-5
+    assert rel(Y2.cpu().double().numpy(), Yo) <= 1e-5
+    assert np.array_equal(Ac2.cpu().numpy(), A.cpu().numpy()[rows])
+    sk.close()
