@@ -180,6 +180,7 @@ id_status launch_pending(id_sketch* h) {
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
     a.wpart = h->d_wpart;
+    a.prefetch = h->prefetch_tiles;
     if (tc) {
       IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, h->nsm, h->drain_blocks, h->d_status,
                                     h->st));
@@ -292,6 +293,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
     if (!strcmp(e, "simt")) h->sketch_kernel = 2;
   }
   if (const char* e = getenv("IDSKETCH_DRAIN_BLOCKS")) h->drain_blocks = std::max(1, atoi(e));
+  if (const char* e = getenv("IDSKETCH_PREFETCH_TILES")) h->prefetch_tiles = std::max(0, atoi(e));
   const int64_t nm = h->n_max;
   const int k = h->k, l = h->l;
   Allocator al;
@@ -317,13 +319,13 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
     al.get(&h->d_F, (size_t)nm * k);
     al.get(&h->d_nu2, (size_t)nm);
     al.get(&h->d_nu20, (size_t)nm);
-    al.get(&h->d_gvec, (size_t)8 * nm);       // row-split partials of A_c^T v_s
-    al.get(&h->d_hvec, (size_t)8 * kLMax);
-    al.get(&h->d_vh, (size_t)h->mc);
-    al.get(&h->d_vl, (size_t)h->mc);
-    al.get(&h->d_upart, (size_t)h->coarse_blocks);
+    al.get(&h->d_gvec, (size_t)h->coarse_blocks * nm);            // row-range partials of A_c^T u
+    al.get(&h->d_hvec, (size_t)kLMax);                             // V_s^T v_s
+    al.get(&h->d_vh, (size_t)h->mc + 8);                           // u below row s, FP32 pair
+    al.get(&h->d_vl, (size_t)h->mc + 8);
+    al.get(&h->d_upart, (size_t)h->coarse_blocks * (kLMax + 1));   // V_s^T u, ||u||^2 partials
     al.get(&h->d_cscal, 8);
-    al.get(&h->d_cint, 4);
+    al.get(&h->d_cint, 8);
     al.get(&h->d_rlist, (size_t)nm);
     al.get(&h->d_Rc, (size_t)k * nm);
     al.get(&h->d_Pc, (size_t)k * nm);

@@ -4,37 +4,52 @@
 // A_c is tall (e.g. 73,728 x 1000), so the QR is LEFT-looking: the
 // reflectors are kept as V (m_c x s) and the trailing matrix is never formed.
 // With F = A^T V T accumulated one column per step (the compact form used by
-// blocked pivoted QR),
-//   A^(s)          = A - V_s F_s^T                      (after s reflectors)
-//   pivot column   u = A(:, p) - V_s F(p, :)^T          (rows >= s)
-//   F(:, s)        = tau_s (A^T v_s - F_s (V_s^T v_s))  (one pass over A_c)
+// blocked pivoted QR), step s with pivot column p computes
+//   u              = A(:, p) - V_s F(p, :)^T          (rows >= s)
+//   v_s            = u / (u_s - beta) below row s, v_s[s] = 1
+//   F(:, s)        = tau_s (A^T v_s - F_s (V_s^T v_s))
 //   R(s, j)        = A(s, j) - V(s, 0:s+1) F(j, 0:s+1)^T
-//   nu_j^2        -= R(s, j)^2                          (norm downdate)
+//   nu_j^2        -= R(s, j)^2                        (norm downdate)
 // A downdated norm that lost more than 20 bits to cancellation is recomputed
 // from its definition ||A^(s+1)(s+1:, j)||^2.  The pivot rule is the largest
 // residual norm, ties to the lowest index; pivoting stops below the rank
-// tolerance.  Reductions run in a fixed order.
+// tolerance.
 //
-// Precision: FP64 throughout, except the one O(m_c n) product per step,
-// A_c^T v_s.  For FP32 data it runs on the FP32 units as exact FP32
-// products of A_c with v_s split into an FP32 pair, summed as FP32 pairs
-// (about 48 significant bits): FP64 arithmetic on this GPU is too slow for a
-// pass over A_c at memory speed, while the FP32 units are not.  Each CTA owns
-// whole columns, so no cross-CTA partial sums are needed.
+// Pass structure (three launches per step).  A^T v_s = A(s, :)^T +
+// (A^T u below row s) / (u_s - beta), so the one O(m_c n) product per step
+// needs u only, not the Householder scalars: step_kernel forms u for its rows
+// and, in the same pass over A_c, the row-range partials of A^T u, V^T u and
+// ||u||^2; the last of its CTAs to finish sums the partials of the scalars.
+// finalize_kernel sums the partials of A^T u per column and updates F, R and
+// the norms; recompute_kernel refreshes flagged norms, and its last CTA picks
+// the next pivot.  Every sum runs in a fixed order (CTA-ordered partials), so
+// results do not depend on scheduling.
+//
+// Precision: FP64 throughout, except the product A_c^T u.  For FP32 data it
+// runs on the FP32 units as exact FP32 products of A_c with u split into an
+// FP32 pair, summed as FP32 pairs (about 48 significant bits): FP64
+// arithmetic on this GPU is too slow for a pass over A_c at memory speed,
+// while the FP32 units are not.
 #include <float.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
 #include "idsk_internal.h"
+#include "tc_common.cuh"
 
 namespace idsk {
 namespace {
 
 constexpr double kRecomputeFrac = 1.0 / (1 << 20);
 // cint layout
-constexpr int CI_P = 0, CI_STOP = 1, CI_NREC = 2, CI_KOUT = 3;
+constexpr int CI_P = 0, CI_STOP = 1, CI_NREC = 2, CI_KOUT = 3, CI_CNT_STEP = 4, CI_CNT_REC = 5,
+              CI_CNT_FIN = 6, CI_PICKED = 7;
 // cscal layout
 constexpr int CS_ALPHA = 0, CS_SIGMA = 1, CS_BETA = 2, CS_TAU = 3, CS_DEN = 4, CS_TOL = 5;
+
+constexpr int ST_THREADS = 256;            // step_kernel block = rows per sub-chunk
+constexpr int HP = kLMax + 1;              // per-CTA partials: V^T u (kLMax), ||u||^2
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -58,6 +73,69 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
+// Pivot of step s over the columns not yet pivoted: largest residual norm
+// (compared as squared norms, which orders the same way), ties to the lowest
+// index.  A non-negative double orders like its IEEE bit pattern read as an
+// unsigned integer, so the comparisons run on the integer units (negative
+// downdated values count as zero).  Whole block; thread 0 records the
+// outcome.
+__device__ __forceinline__ unsigned long long norm_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? 0ull : b;
+}
+
+__device__ void pick_pivot(const double* __restrict__ nu2, int n, int s, int* __restrict__ colpos,
+                           int* __restrict__ Jc, const double* __restrict__ cscal,
+                           int* __restrict__ cint) {
+  __shared__ unsigned long long bv[32];
+  __shared__ int bi[32];
+  unsigned long long v = 0ull;
+  int idx = 0x7fffffff;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (colpos[j] >= 0) continue;
+    const unsigned long long key = norm_key(nu2[j]);
+    if (idx == 0x7fffffff || key > v) {   // j increases within a thread: strict >
+      v = key;
+      idx = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (oi != 0x7fffffff && (idx == 0x7fffffff || ov > v || (ov == v && oi < idx))) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    bv[warp] = v;
+    bi[warp] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = bv[0];
+    int p = bi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      if (bi[w] != 0x7fffffff && (p == 0x7fffffff || bv[w] > b || (bv[w] == b && bi[w] < p))) {
+        b = bv[w];
+        p = bi[w];
+      }
+    }
+    const double tol = cscal[CS_TOL];
+    if (p == 0x7fffffff || !(b > norm_key(tol * tol))) {
+      cint[CI_STOP] = 1;
+      cint[CI_KOUT] = s;
+    } else {
+      cint[CI_P] = p;
+      Jc[s] = p;
+      colpos[p] = s;
+    }
+  }
+}
+
 template <typename T>
 __global__ void init_norms_kernel(const T* __restrict__ Ac, int64_t mc, int n,
                                   double* __restrict__ nu2, double* __restrict__ nu20,
@@ -77,8 +155,11 @@ __global__ void init_norms_kernel(const T* __restrict__ Ac, int64_t mc, int n,
   }
 }
 
-__global__ void init_tol_kernel(const double* __restrict__ nu20, int n, double tol_factor,
-                                double* __restrict__ cscal, int* __restrict__ cint) {
+// Rank tolerance, counters, and the pivot of step 0.
+__global__ void init_tol_kernel(const double* __restrict__ nu20, int n, int kmax,
+                                double tol_factor, int* __restrict__ colpos,
+                                int* __restrict__ Jc, double* __restrict__ cscal,
+                                int* __restrict__ cint) {
   __shared__ double sh[33];
   double ss = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) ss += nu20[j];
@@ -89,138 +170,13 @@ __global__ void init_tol_kernel(const double* __restrict__ nu20, int n, double t
     cint[CI_STOP] = 0;
     cint[CI_NREC] = 0;
     cint[CI_KOUT] = 0;
-  }
-}
-
-__global__ void __launch_bounds__(1024) pick_kernel(const double* __restrict__ nu2, int n, int s,
-                                                    int* __restrict__ colpos,
-                                                    int* __restrict__ Jc,
-                                                    const double* __restrict__ cscal,
-                                                    int* __restrict__ cint) {
-  __shared__ double bv[32];
-  __shared__ int bi[32];
-  if (cint[CI_STOP]) return;
-  double v = -1.0;
-  int idx = 0x7fffffff;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    if (colpos[j] >= 0) continue;
-    const double nu = sqrt(fmax(nu2[j], 0.0));
-    if (nu > v) {   // j increases within a thread: strict > keeps the lowest index
-      v = nu;
-      idx = j;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) {
-      v = ov;
-      idx = oi;
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    bv[warp] = v;
-    bi[warp] = idx;
+    cint[CI_CNT_STEP] = 0;
+    cint[CI_CNT_REC] = 0;
+    cint[CI_CNT_FIN] = 0;
+    cint[CI_PICKED] = 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = bv[0];
-    int p = bi[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      if (bv[w] > b || (bv[w] == b && bi[w] < p)) {
-        b = bv[w];
-        p = bi[w];
-      }
-    }
-    cint[CI_NREC] = 0;
-    if (!(b > cscal[CS_TOL])) {
-      cint[CI_STOP] = 1;
-      cint[CI_KOUT] = s;
-    } else {
-      cint[CI_P] = p;
-      Jc[s] = p;
-      colpos[p] = s;
-    }
-  }
-}
-
-// u = A(:, p) - V_s F(p, 0:s)^T on rows >= s -> V(:, s); partial sums of u_i^2, i > s
-template <typename T>
-__global__ void pivcol_kernel(const T* __restrict__ Ac, int64_t mc, int s,
-                              double* __restrict__ V, const double* __restrict__ F, int64_t ldf,
-                              double* __restrict__ upart, int rows_per_block,
-                              const int* __restrict__ cint) {
-  __shared__ double fp[kLMax];
-  __shared__ double sh[33];
-  if (cint[CI_STOP]) return;
-  const int p = cint[CI_P];
-  for (int t = threadIdx.x; t < s; t += blockDim.x) fp[t] = F[(int64_t)t * ldf + p];
-  __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t r1 = (mc < r0 + rows_per_block) ? mc : r0 + rows_per_block;
-  double ss = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double u = 0.0;
-    if (i >= s) {
-      u = (double)Ac[i + (int64_t)p * mc];
-      for (int t = 0; t < s; ++t) u -= V[(int64_t)t * mc + i] * fp[t];
-      if (i > s) ss += u * u;
-    }
-    V[(int64_t)s * mc + i] = u;
-  }
-  ss = block_sum(ss, sh);
-  if (threadIdx.x == 0) upart[blockIdx.x] = ss;
-}
-
-__global__ void house_kernel(int s, int nblk, double* __restrict__ V, int64_t mc,
-                             const double* __restrict__ upart, double* __restrict__ Rc, int n,
-                             double* __restrict__ cscal, const int* __restrict__ cint) {
-  if (cint[CI_STOP]) return;
-  double part = 0.0;   // fixed order: lane-strided partial sums, then shuffles
-  for (int b = threadIdx.x; b < nblk; b += 32) part += upart[b];
-  const double sigma = warp_sum(part);
-  if (threadIdx.x != 0) return;
-  const int p = cint[CI_P];
-  const double alpha = V[(int64_t)s * mc + s];
-  double beta = alpha, tau = 0.0, den = 0.0;
-  if (sigma != 0.0) {
-    const double nrm = sqrt(alpha * alpha + sigma);
-    beta = alpha >= 0.0 ? -nrm : nrm;
-    tau = (beta - alpha) / beta;
-    den = alpha - beta;
-  }
-  cscal[CS_ALPHA] = alpha;
-  cscal[CS_SIGMA] = sigma;
-  cscal[CS_BETA] = beta;
-  cscal[CS_TAU] = tau;
-  cscal[CS_DEN] = den;
-  V[(int64_t)s * mc + s] = 1.0;
-  Rc[(int64_t)s * n + p] = beta;
-}
-
-// v_s = u / (alpha - beta) on rows > s (written back into V), v_s[s] = 1, and
-// its FP32 pair (hi, lo) for the double-float GEMV below.
-__global__ void scale_kernel(int64_t mc, int s, double* __restrict__ V, float* __restrict__ vh,
-                             float* __restrict__ vl, const double* __restrict__ cscal,
-                             const int* __restrict__ cint) {
-  if (cint[CI_STOP]) return;
-  const double den = cscal[CS_DEN];
-  const double sigma = cscal[CS_SIGMA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mc;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    if (i == s) {
-      v = 1.0;
-    } else if (i > s) {
-      v = sigma != 0.0 ? V[(int64_t)s * mc + i] / den : 0.0;
-      V[(int64_t)s * mc + i] = v;
-    }
-    const float hi = (float)v;
-    vh[i] = hi;
-    vl[i] = (float)(v - (double)hi);
-  }
+  if (kmax > 0) pick_pivot(nu20, n, 0, colpos, Jc, cscal, cint);
 }
 
 // a * (bh + bl) added to the FP32 pair (hi, lo): exact product error by FMA,
@@ -236,81 +192,263 @@ __device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float bh, 
   lo += err + q;
 }
 
-// Partial g_j = A(rows, j)^T v_s for groups of 8 columns and one of RS row
-// ranges per CTA (partials gpart[rs][j], summed in a fixed order by
-// finalize), and partial h_t = V(rows, t)^T v_s for t < s in the CTAs after
-// the column groups.  FP32 data: FP32 products summed as FP32 pairs; FP64
-// data and the h terms: FP64.  The row loop is unrolled by 4 so that 32
-// loads are in flight per thread.
-constexpr int GCOLS = 8;
-constexpr int RS = 8;
+// (hi, lo) += (bh, bl) for FP32 pairs: TwoSum of the high parts, low parts
+// gathered in lo.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float t = hi + bh;
+  const float bp = t - hi;
+  const float err = (hi - (t - bp)) + (bh - bp);
+  hi = t;
+  lo += err + bl;
+}
+
+// True in every thread of the one CTA that finished last (release/acquire
+// through a device-scope counter, which that CTA resets for the next launch).
+__device__ bool last_cta(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Step s over the CTA's row range [r0, r1) of A_c:
+//   * scales column s-1 of V into v_{s-1} (its scalars are final now),
+//   * u = A(:, p) - V_s F(p, :)^T on rows >= s, stored as column s of V and,
+//     below row s, as an FP32 pair (uh, ul) for gemv_kernel (zero elsewhere),
+//   * partials of V_s^T u and ||u||^2 over rows > s.
+// The last CTA sums the partials (fixed CTA order) and forms the Householder
+// scalars alpha = u_s, beta, tau, den = alpha - beta and h = V_s^T v_s.
 template <typename T>
-__global__ void __launch_bounds__(256) gemv_cols_kernel(
-    const T* __restrict__ Ac, int64_t mc, int n, int s, const double* __restrict__ V,
-    const float* __restrict__ vh, const float* __restrict__ vl, int ngroups,
-    double* __restrict__ gpart, double* __restrict__ hpart, const int* __restrict__ cint) {
-  __shared__ double sh[GCOLS][8];
+__global__ void __launch_bounds__(ST_THREADS) step_kernel(
+    const T* __restrict__ Ac, int64_t mc, int n, int s, int64_t rpc,
+    double* __restrict__ V, const double* __restrict__ F, int64_t ldf,
+    float* __restrict__ uh, float* __restrict__ ul, double* __restrict__ hpart,
+    double* __restrict__ hvec, double* __restrict__ Rc, double* __restrict__ cscal,
+    int* __restrict__ cint) {
+  __shared__ double fp[kLMax];
+  __shared__ double ud[ST_THREADS];
+  __shared__ double sh[33];
+  if (cint[CI_STOP]) return;
+  const int p = cint[CI_P];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (blockIdx.x == 0 && tid == 0) cint[CI_PICKED] = 0;   // read by this step's recompute
+  for (int t = tid; t < s; t += ST_THREADS) fp[t] = F[(int64_t)t * ldf + p];
+  const double psig = s > 0 ? cscal[CS_SIGMA] : 0.0;
+  const double prcp = (s > 0 && psig != 0.0) ? 1.0 / cscal[CS_DEN] : 0.0;   // v = u / den
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int64_t r1 = (mc < r0 + rpc) ? mc : r0 + rpc;
+  double sig = 0.0;
+  double hacc[kLMax / 8];
+#pragma unroll
+  for (int q = 0; q < kLMax / 8; ++q) hacc[q] = 0.0;
+  for (int64_t c0 = r0; c0 < r1; c0 += ST_THREADS) {
+    const int nrow = (int)((r1 - c0) < ST_THREADS ? (r1 - c0) : ST_THREADS);
+    const int64_t i = c0 + tid;
+    double uu = 0.0;
+    if (tid < nrow) {
+      if (s > 0) {   // v_{s-1}: zero above row s-1, one at it, u / den below
+        double* vp = V + (int64_t)(s - 1) * mc + i;
+        if (i == s - 1)
+          *vp = 1.0;
+        else if (i > s - 1)
+          *vp *= prcp;
+      }
+      double u = 0.0;
+      if (i >= s) {
+        u = (double)Ac[i + (int64_t)p * mc];
+        for (int t = 0; t < s; ++t) u -= V[(int64_t)t * mc + i] * fp[t];
+      }
+      V[(int64_t)s * mc + i] = u;
+      uu = i > s ? u : 0.0;
+      const float hi = (float)uu;
+      uh[i] = hi;
+      ul[i] = (float)(uu - (double)hi);
+    }
+    ud[tid] = uu;
+    sig += uu * uu;
+    __syncthreads();
+    // V_s^T u: warp w takes t = w + 8q, each lane keeps partials over its rows
+#pragma unroll
+    for (int q = 0; q < kLMax / 8; ++q) {
+      const int t = warp + 8 * q;
+      if (t < s) {
+        const double* vc = V + (int64_t)t * mc + c0;
+        for (int k = lane; k < nrow; k += 32) hacc[q] += vc[k] * ud[k];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kLMax / 8; ++q)
+    if (warp + 8 * q < s) hacc[q] = warp_sum(hacc[q]);
+  sig = block_sum(sig, sh);
+  // partials stored as FP32 pairs (split here, in every CTA, so that the
+  // last CTA sums them on the FP32 units)
+  float2* hp = reinterpret_cast<float2*>(hpart) + (int64_t)blockIdx.x * HP;
+  auto split = [](double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  };
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < kLMax / 8; ++q)
+      if (warp + 8 * q < s) hp[warp + 8 * q] = split(hacc[q]);
+  }
+  if (tid == 0) hp[kLMax] = split(sig);
+  if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_STEP))) return;
+
+  // ---- last CTA: Householder scalars and h = V_s^T v_s.  Warp w sums the
+  // CTA partials of quantities w, w + 8, ... (t < s, and ||u||^2 as quantity
+  // kLMax), lane-strided over the CTAs and then by a fixed shuffle tree.
+  const int G = gridDim.x;
+  __shared__ double hs[kLMax + 1];
+  // The partials are summed as FP32 pairs (TwoSum accumulation, about 48
+  // bits): FP64 adds on this GPU are too slow for a G x (s + 1) reduction on
+  // one SM.
+  constexpr int NQ = kLMax / 8 + 1;   // quantities warp + 8q, q < NQ
+  float ah[NQ], al[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) ah[q] = al[q] = 0.f;
+  for (int b = lane; b < G; b += 32) {   // all loads of an iteration in flight
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int qn = warp + 8 * q;
+      if (qn < s || qn == kLMax) {
+        const float2 x = reinterpret_cast<const float2*>(hpart)[(int64_t)b * HP + qn];
+        df_add(ah[q], al[q], x.x, x.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int qn = warp + 8 * q;
+    if (qn < s || qn == kLMax) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, ah[q], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, al[q], o);
+        df_add(ah[q], al[q], oh, ol);
+      }
+      if (lane == 0) hs[qn] = (double)ah[q] + (double)al[q];
+    }
+  }
+  __syncthreads();
+  const double sigma = hs[kLMax];
+  const double alpha = V[(int64_t)s * mc + s];
+  double beta = alpha, tau = 0.0, den = 0.0;
+  if (sigma != 0.0) {
+    const double nrm = sqrt(alpha * alpha + sigma);
+    beta = alpha >= 0.0 ? -nrm : nrm;
+    tau = (beta - alpha) / beta;
+    den = alpha - beta;
+  }
+  const double rden = sigma != 0.0 ? 1.0 / den : 0.0;
+  for (int t = tid; t < s; t += ST_THREADS) {
+    const double vst = V[(int64_t)t * mc + s];   // v_t[s]
+    hvec[t] = vst + hs[t] * rden;
+  }
+  if (tid == 0) {
+    cscal[CS_ALPHA] = alpha;
+    cscal[CS_SIGMA] = sigma;
+    cscal[CS_BETA] = beta;
+    cscal[CS_TAU] = tau;
+    cscal[CS_DEN] = den;
+    Rc[(int64_t)s * n + p] = beta;
+  }
+}
+
+// Partial g_j = A(rows, j)^T u for a group of GCOLS columns and one of RS
+// row ranges per CTA (gpart[rs][j], summed in a fixed order by
+// finalize_kernel).  Lanes take consecutive row quads (128-bit loads, two row
+// quads of every column in flight per thread); FP32 data: exact FP32
+// products with u as an FP32 pair, summed as FP32 pairs; FP64 data: FP64.
+constexpr int GCOLS = 8;
+constexpr int GV_THREADS = 256;
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS) gemv_kernel(
+    const T* __restrict__ Ac, int64_t mc, int n, int s, int64_t chunk, int vec,
+    const float* __restrict__ uh, const float* __restrict__ ul, const double* __restrict__ V,
+    double* __restrict__ gpart, const int* __restrict__ cint) {
+  __shared__ double sh[GCOLS][GV_THREADS / 32];
   if (cint[CI_STOP]) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t span = mc - s;
-  const int64_t chunk = (span + RS - 1) / RS;
-  if ((int)blockIdx.x >= ngroups * RS) {   // partial h_t
-    const int b = blockIdx.x - ngroups * RS;
-    const int t = b / RS, rs = b - t * RS;
-    const int64_t i0 = s + rs * chunk, i1 = min(mc, i0 + chunk);
-    double acc = 0.0;
-    const double* col = V + (int64_t)t * mc;
-    for (int64_t i = i0 + tid; i < i1; i += 256) acc += col[i] * ((double)vh[i] + (double)vl[i]);
-    acc = warp_sum(acc);
-    if (lane == 0) sh[0][warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double r = 0.0;
-      for (int w = 0; w < 8; ++w) r += sh[0][w];
-      hpart[rs * kLMax + t] = r;
-    }
-    return;
-  }
-  const int grp = blockIdx.x / RS, rs = blockIdx.x - grp * RS;
-  const int64_t i0 = s + rs * chunk, i1 = min(mc, i0 + chunk);
+  const int ngroups = (n + GCOLS - 1) / GCOLS;
+  const int grp = blockIdx.x % ngroups, rs = blockIdx.x / ngroups;
   const int j0 = grp * GCOLS;
+  // rows above s + 1 hold u = 0: start at the row quad holding s + 1
+  int64_t i0 = rs * chunk, i1 = i0 + chunk < mc ? i0 + chunk : mc;
+  const int64_t lo_row = (int64_t)(s + 1) & ~(int64_t)3;
+  if (i0 < lo_row) i0 = lo_row < i1 ? lo_row : i1;
   const T* cols[GCOLS];
 #pragma unroll
-  for (int q = 0; q < GCOLS; ++q) cols[q] = Ac + (int64_t)min(j0 + q, n - 1) * mc;
+  for (int q = 0; q < GCOLS; ++q) cols[q] = Ac + (int64_t)(j0 + q < n ? j0 + q : n - 1) * mc;
   double r[GCOLS];
-  if (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
     float hi[GCOLS], lo[GCOLS];
 #pragma unroll
     for (int q = 0; q < GCOLS; ++q) hi[q] = lo[q] = 0.f;
-    int64_t i = i0 + tid;
-    for (; i + 3 * 256 < i1; i += 4 * 256) {
-      float a[4][GCOLS], bh[4], bl[4];
+    if (vec) {   // mc, chunk multiples of 4
+      int64_t i = i0 + 4 * tid;
+      for (; i + 4 * GV_THREADS < i1; i += 8 * GV_THREADS) {
+        float4 x0[GCOLS], x1[GCOLS];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        bh[u] = vh[i + u * 256];
-        bl[u] = vl[i + u * 256];
+        for (int q = 0; q < GCOLS; ++q) {
+          x0[q] = __ldcs(reinterpret_cast<const float4*>(cols[q] + i));
+          x1[q] = __ldcs(reinterpret_cast<const float4*>(cols[q] + i + 4 * GV_THREADS));
+        }
+        const float4 h0 = *reinterpret_cast<const float4*>(uh + i);
+        const float4 l0 = *reinterpret_cast<const float4*>(ul + i);
+        const float4 h1 = *reinterpret_cast<const float4*>(uh + i + 4 * GV_THREADS);
+        const float4 l1 = *reinterpret_cast<const float4*>(ul + i + 4 * GV_THREADS);
 #pragma unroll
-        for (int q = 0; q < GCOLS; ++q) a[u][q] = (float)cols[q][i + u * 256];
+        for (int q = 0; q < GCOLS; ++q) {
+          df_acc(hi[q], lo[q], x0[q].x, h0.x, l0.x);
+          df_acc(hi[q], lo[q], x0[q].y, h0.y, l0.y);
+          df_acc(hi[q], lo[q], x0[q].z, h0.z, l0.z);
+          df_acc(hi[q], lo[q], x0[q].w, h0.w, l0.w);
+          df_acc(hi[q], lo[q], x1[q].x, h1.x, l1.x);
+          df_acc(hi[q], lo[q], x1[q].y, h1.y, l1.y);
+          df_acc(hi[q], lo[q], x1[q].z, h1.z, l1.z);
+          df_acc(hi[q], lo[q], x1[q].w, h1.w, l1.w);
+        }
       }
+      for (; i < i1; i += 4 * GV_THREADS) {
+        const float4 h0 = *reinterpret_cast<const float4*>(uh + i);
+        const float4 l0 = *reinterpret_cast<const float4*>(ul + i);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+        for (int q = 0; q < GCOLS; ++q) {
+          const float4 x = __ldcs(reinterpret_cast<const float4*>(cols[q] + i));
+          df_acc(hi[q], lo[q], x.x, h0.x, l0.x);
+          df_acc(hi[q], lo[q], x.y, h0.y, l0.y);
+          df_acc(hi[q], lo[q], x.z, h0.z, l0.z);
+          df_acc(hi[q], lo[q], x.w, h0.w, l0.w);
+        }
+      }
+    } else {
+      for (int64_t i = i0 + tid; i < i1; i += GV_THREADS) {
+        const float bh = uh[i], bl = ul[i];
 #pragma unroll
-        for (int q = 0; q < GCOLS; ++q) df_acc(hi[q], lo[q], a[u][q], bh[u], bl[u]);
-    }
-    for (; i < i1; i += 256) {
-      const float bh = vh[i], bl = vl[i];
-#pragma unroll
-      for (int q = 0; q < GCOLS; ++q) df_acc(hi[q], lo[q], (float)cols[q][i], bh, bl);
+        for (int q = 0; q < GCOLS; ++q) df_acc(hi[q], lo[q], cols[q][i], bh, bl);
+      }
     }
 #pragma unroll
     for (int q = 0; q < GCOLS; ++q) r[q] = (double)hi[q] + (double)lo[q];
   } else {
+    const double* u = V + (int64_t)s * mc;   // zero at and above row s is masked below
 #pragma unroll
     for (int q = 0; q < GCOLS; ++q) r[q] = 0.0;
-    for (int64_t i = i0 + tid; i < i1; i += 256) {
-      const double b = (double)vh[i] + (double)vl[i];
+    for (int64_t i = i0 + tid; i < i1; i += GV_THREADS) {
+      const double b = i > s ? u[i] : 0.0;
 #pragma unroll
-      for (int q = 0; q < GCOLS; ++q) r[q] += (double)cols[q][i] * b;
+      for (int q = 0; q < GCOLS; ++q) r[q] = fma((double)cols[q][i], b, r[q]);
     }
   }
 #pragma unroll
@@ -321,66 +459,301 @@ __global__ void __launch_bounds__(256) gemv_cols_kernel(
   __syncthreads();
   if (tid < GCOLS && j0 + tid < n) {
     double acc = 0.0;
-    for (int w = 0; w < 8; ++w) acc += sh[tid][w];
+    for (int w = 0; w < GV_THREADS / 32; ++w) acc += sh[tid][w];
     gpart[(int64_t)rs * n + j0 + tid] = acc;
   }
 }
 
-template <typename T>
-__global__ void finalize_kernel(const T* __restrict__ Ac, int64_t mc, int n, int s,
-                                const double* __restrict__ V, double* __restrict__ F, int64_t ldf,
-                                const double* __restrict__ gpart, const double* __restrict__ hpart,
-                                const int* __restrict__ colpos, double* __restrict__ Rc,
-                                double* __restrict__ nu2, const double* __restrict__ nu20,
-                                int* __restrict__ rlist, const double* __restrict__ cscal,
-                                int* __restrict__ cint) {
-  __shared__ double h[kLMax];
-  __shared__ double vrow[kLMax + 1];
-  if (cint[CI_STOP]) return;
-  for (int t = threadIdx.x; t < s; t += blockDim.x) {
-    double acc = 0.0;
-    for (int rs = 0; rs < RS; ++rs) acc += hpart[rs * kLMax + t];
-    h[t] = acc;
-  }
-  for (int t = threadIdx.x; t <= s; t += blockDim.x) vrow[t] = V[(int64_t)t * mc + s];
-  __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int cp = colpos[j];
-  if (cp >= 0) {
-    if (cp < s) Rc[(int64_t)s * n + j] = 0.0;   // R(s, p) itself was set with beta
-    return;
-  }
-  const double tau = cscal[CS_TAU];
-  double fh = 0.0;
-  for (int t = 0; t < s; ++t) fh += F[(int64_t)t * ldf + j] * h[t];
-  double gj = 0.0;
-  for (int rs = 0; rs < RS; ++rs) gj += gpart[(int64_t)rs * n + j];
-  const double fjs = tau * (gj - fh);
-  F[(int64_t)s * ldf + j] = fjs;
-  double r = (double)Ac[s + (int64_t)j * mc];
-  for (int t = 0; t < s; ++t) r -= vrow[t] * F[(int64_t)t * ldf + j];
-  r -= vrow[s] * fjs;
-  Rc[(int64_t)s * n + j] = r;
-  const double nn = nu2[j] - r * r;
-  nu2[j] = nn;
-  if (nn <= kRecomputeFrac * nu20[j]) {
-    const int slot = atomicAdd(&cint[CI_NREC], 1);
-    rlist[slot] = j;
-  }
+// Streamed pass over FP32 A_c (m_c a multiple of 4): A_c^T u below row s
+// (mode 0, u as the FP32 pair uh + ul) or the column sums of squares (mode 1).
+// Work items are (group of SG_COLS columns, chunk of SG_ROWS rows) in
+// group-major order; CTA b takes the contiguous item range
+// [T b / G, T (b + 1) / G).  One producer thread bulk-copies each item's
+// column pieces (and u's pair) into an SG_ST-stage shared-memory ring; eight
+// consumer warps (thread t: row quads t, t + 256, ...) accumulate FP32-pair
+// sums over the chunks of a group and, when the group changes, write one
+// partial per (CTA, column): part[b][j].  stream_cta_range() gives the CTAs
+// that touched a column, whose partials are then summed in CTA order.
+constexpr int SG_COLS = 4, SG_ROWS = 4096, SG_ST = 2, SG_CONS = 8;
+constexpr uint32_t SG_COLB = SG_ROWS * 4;                  // 16 KB column piece
+constexpr uint32_t SG_STAGE = (SG_COLS + 2) * SG_COLB;     // + uh, ul
+constexpr int SG_THREADS = (SG_CONS + 1) * 32;
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
 }
 
-// nu_j^2 = ||A^(s+1)(s+1:, j)||^2 from the definition, for the flagged columns
+__device__ __forceinline__ void mbar_expect_tx_arrive(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// CTAs [*b0, *b1] whose item ranges hold the items of column group g.
+__host__ __device__ inline void stream_cta_range(int64_t T, int G, int64_t nchunks, int g,
+                                                 int* b0, int* b1) {
+  auto cta_of = [&](int64_t item) {
+    int64_t b = item * G / T;
+    while (b + 1 < G && T * (b + 1) / G <= item) ++b;
+    while (b > 0 && T * b / G > item) --b;
+    return (int)b;
+  };
+  *b0 = cta_of((int64_t)g * nchunks);
+  *b1 = cta_of((int64_t)(g + 1) * nchunks - 1);
+}
+
+__global__ void __launch_bounds__(SG_THREADS, 1) stream_gemv_kernel(
+    const float* __restrict__ Ac, int64_t mc, int n, int mode, const float* __restrict__ uh,
+    const float* __restrict__ ul, double* __restrict__ part, int* __restrict__ status,
+    const int* __restrict__ cint) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * SG_ST];
+  __shared__ int abort_flag;
+  __shared__ double red[SG_CONS][SG_COLS];
+  if (mode == 0 && cint[CI_STOP]) return;
+  const uint32_t base = (tc::smem_u32(smem_raw) + 127u) & ~127u;
+  const uint8_t* basep = smem_raw + (base - tc::smem_u32(smem_raw));
+  const uint32_t full0 = tc::smem_u32(&bars[0]), empty0 = tc::smem_u32(&bars[SG_ST]);
+  const uint32_t abort_a = tc::smem_u32(&abort_flag);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ngroups = (n + SG_COLS - 1) / SG_COLS;
+  const int64_t nchunks = (mc + SG_ROWS - 1) / SG_ROWS;
+  const int64_t T = (int64_t)ngroups * nchunks;
+  const int64_t it0 = T * blockIdx.x / gridDim.x, it1 = T * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    for (int q = 0; q < SG_ST; ++q) {
+      tc::mbar_init(full0 + 8u * q, 1);
+      tc::mbar_init(empty0 + 8u * q, SG_CONS);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == SG_CONS) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      int u = 0;
+      for (int64_t it = it0; it < it1; ++it, ++u) {
+        const int st = u % SG_ST;
+        if (u >= SG_ST && !tc::mbar_wait_spin(empty0 + 8u * st, ((u / SG_ST) - 1) & 1, abort_a))
+          break;
+        const int g = (int)(it / nchunks);
+        const int64_t r0 = (it - (int64_t)g * nchunks) * SG_ROWS;
+        const uint32_t bytes = (uint32_t)((mc - r0 < SG_ROWS ? mc - r0 : SG_ROWS) * 4);
+        const int ncols = n - g * SG_COLS < SG_COLS ? n - g * SG_COLS : SG_COLS;
+        const uint32_t dst = base + (uint32_t)st * SG_STAGE;
+        mbar_expect_tx_arrive(full0 + 8u * st, bytes * (ncols + (mode == 0 ? 2 : 0)));
+        for (int q = 0; q < ncols; ++q)
+          bulk_g2s(dst + q * SG_COLB, Ac + (int64_t)(g * SG_COLS + q) * mc + r0, bytes,
+                   full0 + 8u * st);
+        if (mode == 0) {
+          bulk_g2s(dst + SG_COLS * SG_COLB, uh + r0, bytes, full0 + 8u * st);
+          bulk_g2s(dst + (SG_COLS + 1) * SG_COLB, ul + r0, bytes, full0 + 8u * st);
+        }
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- consumers
+    float hi[SG_COLS], lo[SG_COLS];
+    int cur = -1;
+    auto flush = [&](int g) {
+#pragma unroll
+      for (int q = 0; q < SG_COLS; ++q) {
+        double v = (double)hi[q] + (double)lo[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(SG_CONS * 32) : "memory");
+      if (tid < SG_COLS && g * SG_COLS + tid < n) {
+        double a = 0.0;
+        for (int w = 0; w < SG_CONS; ++w) a += red[w][tid];
+        part[(int64_t)blockIdx.x * n + g * SG_COLS + tid] = a;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(SG_CONS * 32) : "memory");
+    };
+    // one row quad of the stage into the accumulators
+    auto quad = [&](const uint8_t* stage, int ncols, int r4) {
+      float4 bh = make_float4(0.f, 0.f, 0.f, 0.f), bl = bh;
+      if (mode == 0) {
+        bh = *reinterpret_cast<const float4*>(stage + SG_COLS * SG_COLB + 4 * r4);
+        bl = *reinterpret_cast<const float4*>(stage + (SG_COLS + 1) * SG_COLB + 4 * r4);
+      }
+      float4 x[SG_COLS];
+#pragma unroll
+      for (int q = 0; q < SG_COLS; ++q)
+        x[q] = q < ncols ? *reinterpret_cast<const float4*>(stage + q * SG_COLB + 4 * r4)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < SG_COLS; ++q) {
+        if (mode == 0) {
+          df_acc(hi[q], lo[q], x[q].x, bh.x, bl.x);
+          df_acc(hi[q], lo[q], x[q].y, bh.y, bl.y);
+          df_acc(hi[q], lo[q], x[q].z, bh.z, bl.z);
+          df_acc(hi[q], lo[q], x[q].w, bh.w, bl.w);
+        } else {
+          df_acc(hi[q], lo[q], x[q].x, x[q].x, 0.f);
+          df_acc(hi[q], lo[q], x[q].y, x[q].y, 0.f);
+          df_acc(hi[q], lo[q], x[q].z, x[q].z, 0.f);
+          df_acc(hi[q], lo[q], x[q].w, x[q].w, 0.f);
+        }
+      }
+    };
+    int u = 0;
+    for (int64_t it = it0; it < it1; ++it, ++u) {
+      const int st = u % SG_ST;
+      const int g = (int)(it / nchunks);
+      if (g != cur) {
+        if (cur >= 0) flush(cur);
+        cur = g;
+#pragma unroll
+        for (int q = 0; q < SG_COLS; ++q) hi[q] = lo[q] = 0.f;
+      }
+      // after a timeout every consumer keeps the same loop (and flushes) but
+      // skips the data, so that the named barriers in flush() stay matched
+      const bool ok = tc::mbar_wait_spin(full0 + 8u * st, (u / SG_ST) & 1, abort_a);
+      const int64_t r0 = (it - (int64_t)g * nchunks) * SG_ROWS;
+      const int rows = (int)(mc - r0 < SG_ROWS ? mc - r0 : SG_ROWS);
+      const int ncols = n - g * SG_COLS < SG_COLS ? n - g * SG_COLS : SG_COLS;
+      const uint8_t* stage = basep + (size_t)st * SG_STAGE;
+      for (int r4 = 4 * tid; ok && r4 < rows; r4 += 4 * SG_CONS * 32) quad(stage, ncols, r4);
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(empty0 + 8u * st);
+    }
+    if (cur >= 0) flush(cur);
+  }
+  __syncthreads();
+  if (tid == 0 && abort_flag) atomicOr(status, 1);
+}
+
+// Column norms from the streamed sums of squares: nu2 = nu20 = sum over the
+// CTAs that touched the column, in CTA order.
+__global__ void norms_from_parts_kernel(const double* __restrict__ part, int64_t mc, int n, int G,
+                                        double* __restrict__ nu2, double* __restrict__ nu20,
+                                        int* __restrict__ colpos) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int ngroups = (n + SG_COLS - 1) / SG_COLS;
+  const int64_t nchunks = (mc + SG_ROWS - 1) / SG_ROWS;
+  int b0, b1;
+  stream_cta_range((int64_t)ngroups * nchunks, G, nchunks, j / SG_COLS, &b0, &b1);
+  double a = 0.0;
+  for (int b = b0; b <= b1; ++b) a += part[(int64_t)b * n + j];
+  nu2[j] = a;
+  nu20[j] = a;
+  colpos[j] = -1;
+}
+
+// Per column j (lane of warp 0): g_j = A(:, j)^T v_s from the CTA-ordered
+// partials (G > 0: G row-split partials summed by the 8 warps over contiguous
+// ranges, then in warp order; G < 0: the streamed partials of the -G CTAs of
+// stream_gemv_kernel that touched the column), F(j, s), R(s, j) and the norm
+// downdate.
+constexpr int FIN_COLS = 32;
 template <typename T>
-__global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int s,
+__global__ void __launch_bounds__(256) finalize_kernel(
+    const T* __restrict__ Ac, int64_t mc, int n, int s, int G, const double* __restrict__ V,
+    double* __restrict__ F, int64_t ldf, const double* __restrict__ gpart,
+    const double* __restrict__ hvec, int* __restrict__ colpos, double* __restrict__ Rc,
+    double* __restrict__ nu2, const double* __restrict__ nu20, int* __restrict__ rlist,
+    int kmax, int* __restrict__ Jc, const double* __restrict__ cscal, int* __restrict__ cint) {
+  __shared__ double part[8][FIN_COLS];
+  __shared__ double pfh[8][FIN_COLS];
+  __shared__ double prr[8][FIN_COLS];
+  __shared__ double h[kLMax];
+  __shared__ double vrow[kLMax];
+  if (cint[CI_STOP]) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int j = blockIdx.x * FIN_COLS + lane;
+  if (G > 0) {   // RS row-split partials: warp w sums a contiguous range
+    const int b0 = (int)((int64_t)G * warp / 8), b1 = (int)((int64_t)G * (warp + 1) / 8);
+    double a = 0.0;
+    if (j < n)
+      for (int b = b0; b < b1; ++b) a += gpart[(int64_t)b * n + j];
+    part[warp][lane] = a;
+  } else {       // streamed partials of the CTAs that touched column j
+    double a = 0.0;
+    if (warp == 0 && j < n) {
+      const int ngroups = (n + SG_COLS - 1) / SG_COLS;
+      const int64_t nchunks = (mc + SG_ROWS - 1) / SG_ROWS;
+      int b0, b1;
+      stream_cta_range((int64_t)ngroups * nchunks, -G, nchunks, j / SG_COLS, &b0, &b1);
+      for (int b = b0; b <= b1; ++b) a += gpart[(int64_t)b * n + j];
+    }
+    part[warp][lane] = a;
+  }
+  for (int t = tid; t < s; t += 256) {
+    h[t] = hvec[t];
+    vrow[t] = V[(int64_t)t * mc + s];
+  }
+  __syncthreads();
+  // F(j, 0:s) h and V(s, 0:s) F(j, 0:s)^T: warp w takes t = w, w + 8, ...
+  {
+    double fh = 0.0, rr = 0.0;
+    if (j < n)
+      for (int t = warp; t < s; t += 8) {
+        const double f = F[(int64_t)t * ldf + j];
+        fh += f * h[t];
+        rr += vrow[t] * f;
+      }
+    pfh[warp][lane] = fh;
+    prr[warp][lane] = rr;
+  }
+  __syncthreads();
+  if (warp == 0 && j < n) {
+    double gsum = 0.0, fh = 0.0, rr = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      gsum += part[w][lane];
+      fh += pfh[w][lane];
+      rr += prr[w][lane];
+    }
+    const int cp = colpos[j];
+    if (cp >= 0) {
+      if (cp < s) Rc[(int64_t)s * n + j] = 0.0;   // R(s, p) itself was set with beta
+    } else {
+      const double tau = cscal[CS_TAU], den = cscal[CS_DEN], sigma = cscal[CS_SIGMA];
+      const double asj = (double)Ac[s + (int64_t)j * mc];
+      const double gj = sigma != 0.0 ? asj + gsum / den : asj;
+      const double fjs = tau * (gj - fh);
+      F[(int64_t)s * ldf + j] = fjs;
+      const double r = asj - rr - fjs;   // v_s[s] = 1
+      Rc[(int64_t)s * n + j] = r;
+      const double nn = nu2[j] - r * r;
+      nu2[j] = nn;
+      if (nn <= kRecomputeFrac * nu20[j]) {
+        const int slot = atomicAdd(&cint[CI_NREC], 1);
+        rlist[slot] = j;
+      }
+    }
+  }
+  // the last CTA picks the next pivot unless a norm needs recomputing first
+  if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_FIN))) return;
+  if (cint[CI_NREC] != 0) return;
+  if (s + 1 < kmax) pick_pivot(nu2, n, s + 1, colpos, Jc, cscal, cint);
+  if (tid == 0) cint[CI_PICKED] = 1;
+}
+
+// nu_j^2 = ||A^(s+1)(s+1:, j)||^2 from the definition, for the flagged
+// columns (column s of V still holds u: v_s = u / den below row s); the last
+// CTA then picks the pivot of step s + 1.
+template <typename T>
+__global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int n, int s, int kmax,
                                  const double* __restrict__ V, const double* __restrict__ F,
                                  int64_t ldf, const int* __restrict__ rlist,
                                  double* __restrict__ nu2, double* __restrict__ nu20,
-                                 const int* __restrict__ cint) {
+                                 int* __restrict__ colpos, int* __restrict__ Jc,
+                                 const double* __restrict__ cscal, int* __restrict__ cint) {
   __shared__ double fj[kLMax + 1];
   __shared__ double sh[33];
   if (cint[CI_STOP]) return;
+  if (cint[CI_PICKED]) return;   // finalize_kernel found nothing to recompute and picked
   const int nrec = cint[CI_NREC];
+  const double sigma = cscal[CS_SIGMA];
+  const double rden = sigma != 0.0 ? 1.0 / cscal[CS_DEN] : 0.0;
   for (int idx = blockIdx.x; idx < nrec; idx += gridDim.x) {
     const int j = rlist[idx];
     __syncthreads();
@@ -389,7 +762,9 @@ __global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int s,
     double ss = 0.0;
     for (int64_t i = s + 1 + threadIdx.x; i < mc; i += blockDim.x) {
       double a = (double)Ac[i + (int64_t)j * mc];
-      for (int t = 0; t <= s; ++t) a -= V[(int64_t)t * mc + i] * fj[t];
+      for (int t = 0; t < s; ++t) a -= V[(int64_t)t * mc + i] * fj[t];
+      const double vs = V[(int64_t)s * mc + i] * rden;
+      a -= vs * fj[s];
       ss += a * a;
     }
     ss = block_sum(ss, sh);
@@ -398,12 +773,37 @@ __global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int s,
       nu20[j] = ss;
     }
   }
+  if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_REC))) return;
+  if (threadIdx.x == 0) cint[CI_NREC] = 0;
+  if (s + 1 < kmax) pick_pivot(nu2, n, s + 1, colpos, Jc, cscal, cint);
 }
 
 __global__ void coarse_done_kernel(int kmax, int k, int* __restrict__ Jc, int* __restrict__ cint) {
   if (threadIdx.x == 0 && !cint[CI_STOP]) cint[CI_KOUT] = kmax;
   __syncthreads();
   for (int q = cint[CI_KOUT] + threadIdx.x; q < k; q += blockDim.x) Jc[q] = -1;
+}
+
+// Row ranges of step_kernel: G CTAs of rpc rows (a multiple of 4).
+void step_grid(int64_t mc, int nsm, int* G, int64_t* rpc) {
+  int64_t g = (mc + 63) / 64;   // at least 64 rows per CTA, two CTAs per SM at most
+  g = std::max<int64_t>(1, std::min<int64_t>(g, 2 * (int64_t)nsm));
+  int64_t r = (mc + g - 1) / g;
+  r = (r + 3) / 4 * 4;
+  *rpc = r;
+  *G = (int)((mc + r - 1) / r);
+}
+
+// Row splits of gemv_kernel: about seven waves of two CTAs per SM over the
+// column groups, rows split in multiples of 4.
+void gemv_grid(int64_t mc, int n, int nsm, int max_rs, int* RS, int64_t* chunk) {
+  const int ngroups = (n + GCOLS - 1) / GCOLS;
+  int rs = (14 * nsm + ngroups - 1) / ngroups;
+  rs = std::max(1, std::min(rs, max_rs));
+  int64_t c = (mc + rs - 1) / rs;
+  c = std::max<int64_t>(4, (c + 3) / 4 * 4);
+  *chunk = c;
+  *RS = (int)((mc + c - 1) / c);
 }
 
 template <typename T>
@@ -414,35 +814,57 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   const int k = h->k;
   const int kmax = (int)std::min<int64_t>(k, std::min<int64_t>(mc, n64));
   const int64_t ldf = h->n_max;
+  int G, RS;
+  int64_t rpc, chunk;
+  step_grid(mc, h->nsm, &G, &rpc);
+  gemv_grid(mc, n, h->nsm, h->coarse_blocks, &RS, &chunk);
+  if (G > h->coarse_blocks || RS > h->coarse_blocks || h->nsm > h->coarse_blocks)
+    return cudaErrorInvalidValue;
+  const int vec = (sizeof(T) == 4 && (mc & 3) == 0) ? 1 : 0;
   const int ngroups = (n + GCOLS - 1) / GCOLS;
-  int rpb = (int)((mc + 2 * h->nsm - 1) / (2 * h->nsm));
-  rpb = std::max(32, ((rpb + 31) / 32) * 32);
-  rpb = std::min(rpb, 4096);
-  const int nblk = (int)((mc + rpb - 1) / rpb);
-  if (nblk > h->coarse_blocks) return cudaErrorInvalidValue;
+  const int fin_blocks = (n + FIN_COLS - 1) / FIN_COLS;
 
-  init_norms_kernel<T><<<n, 256, 0, st>>>(Ac, mc, n, h->d_nu2, h->d_nu20, h->d_colposc);
-  init_tol_kernel<<<1, 1024, 0, st>>>(h->d_nu20, n, ID_RANK_TOL_FACTOR, h->d_cscal, h->d_cint);
+  // FP32 data with m_c a multiple of 4 streams A_c through bulk copies
+  const bool streamed = vec && getenv("IDSKETCH_COARSE_STREAM") == nullptr;
+  const int SG = h->nsm;
+  const size_t sg_smem = 128 + (size_t)SG_ST * SG_STAGE;
+  if (streamed) {
+    cudaError_t e0 = cudaFuncSetAttribute(stream_gemv_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sg_smem);
+    if (e0 != cudaSuccess) return e0;
+    stream_gemv_kernel<<<SG, SG_THREADS, sg_smem, st>>>(
+        reinterpret_cast<const float*>(Ac), mc, n, 1, nullptr, nullptr, h->d_gvec, h->d_status,
+        h->d_cint);
+    norms_from_parts_kernel<<<(n + 255) / 256, 256, 0, st>>>(h->d_gvec, mc, n, SG, h->d_nu2,
+                                                             h->d_nu20, h->d_colposc);
+  } else {
+    init_norms_kernel<T><<<n, 256, 0, st>>>(Ac, mc, n, h->d_nu2, h->d_nu20, h->d_colposc);
+  }
+  init_tol_kernel<<<1, 1024, 0, st>>>(h->d_nu20, n, kmax, ID_RANK_TOL_FACTOR, h->d_colposc,
+                                      h->d_Jc, h->d_cscal, h->d_cint);
   count_launches(2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < kmax; ++s) {
-    pick_kernel<<<1, 1024, 0, st>>>(h->d_nu2, n, s, h->d_colposc, h->d_Jc, h->d_cscal, h->d_cint);
-    pivcol_kernel<T><<<nblk, 256, 0, st>>>(Ac, mc, s, h->d_V, h->d_F, ldf, h->d_upart, rpb,
-                                           h->d_cint);
-    house_kernel<<<1, 32, 0, st>>>(s, nblk, h->d_V, mc, h->d_upart, h->d_Rc, n, h->d_cscal,
-                                   h->d_cint);
-    scale_kernel<<<2 * h->nsm, 256, 0, st>>>(mc, s, h->d_V, h->d_vh, h->d_vl, h->d_cscal,
-                                             h->d_cint);
-    gemv_cols_kernel<T><<<(ngroups + s) * RS, 256, 0, st>>>(Ac, mc, n, s, h->d_V, h->d_vh,
-                                                            h->d_vl, ngroups, h->d_gvec,
-                                                            h->d_hvec, h->d_cint);
-    finalize_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(
-        Ac, mc, n, s, h->d_V, h->d_F, ldf, h->d_gvec, h->d_hvec, h->d_colposc, h->d_Rc,
-        h->d_nu2, h->d_nu20, h->d_rlist, h->d_cscal, h->d_cint);
-    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, s, h->d_V, h->d_F, ldf, h->d_rlist, h->d_nu2,
-                                            h->d_nu20, h->d_cint);
-    count_launches(7);
+    step_kernel<T><<<G, ST_THREADS, 0, st>>>(Ac, mc, n, s, rpc, h->d_V, h->d_F, ldf, h->d_vh,
+                                             h->d_vl, h->d_upart, h->d_hvec, h->d_Rc,
+                                             h->d_cscal, h->d_cint);
+    if (streamed)
+      stream_gemv_kernel<<<SG, SG_THREADS, sg_smem, st>>>(
+          reinterpret_cast<const float*>(Ac), mc, n, 0, h->d_vh, h->d_vl, h->d_gvec,
+          h->d_status, h->d_cint);
+    else
+      gemv_kernel<T><<<ngroups * RS, GV_THREADS, 0, st>>>(Ac, mc, n, s, chunk, vec, h->d_vh,
+                                                          h->d_vl, h->d_V, h->d_gvec, h->d_cint);
+    finalize_kernel<T><<<fin_blocks, 256, 0, st>>>(
+        Ac, mc, n, s, streamed ? -SG : RS, h->d_V, h->d_F, ldf, h->d_gvec, h->d_hvec,
+        h->d_colposc, h->d_Rc, h->d_nu2, h->d_nu20, h->d_rlist, kmax, h->d_Jc, h->d_cscal,
+        h->d_cint);
+    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, n, s, kmax, h->d_V, h->d_F, ldf, h->d_rlist,
+                                            h->d_nu2, h->d_nu20, h->d_colposc, h->d_Jc,
+                                            h->d_cscal, h->d_cint);
+    count_launches(4);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -460,11 +882,13 @@ cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st) {
   return run<float>(h, n, st);
 }
 
+// Rows of the per-CTA partial buffers: step_kernel's CTAs, and one per SM for
+// stream_gemv_kernel.
 int coarse_blocks_needed(int64_t mc, int nsm) {
-  int rpb = (int)((mc + 2 * nsm - 1) / (2 * nsm));
-  rpb = std::max(32, ((rpb + 31) / 32) * 32);
-  rpb = std::min(rpb, 4096);
-  return (int)((mc + rpb - 1) / rpb);
+  int G;
+  int64_t rpc;
+  step_grid(mc, nsm, &G, &rpc);
+  return std::max(G, nsm);
 }
 
 }  // namespace idsk

@@ -8,14 +8,25 @@
 // pivots and R in exact arithmetic and are the stabler choice.
 //
 // Pivot rule: the largest residual column norm ||W^(s)(s:, j)||, recomputed
-// from the updated matrix at every step (no downdating), ties to the lowest
-// column index.  One CTA of 1024 threads works in place on a copy of W held
-// row-major in global memory (L2-resident: l x n x 8 bytes); thread t owns
-// columns t, t + 1024, ...  Norms and the argmax use warp shuffles; the
-// reflector of the pivot column is formed by one warp.
+// from the updated matrix at every step (no downdating) and compared as its
+// square, ties to the lowest column index.
+//
+// n <= 1024 (cpqr_cluster_kernel): a cluster of 8 CTAs x 128 threads, one
+// column per thread held in registers for the whole factorization.  Per
+// step, each CTA's best candidate and then the pivot column are published in
+// its shared memory and read by the other CTAs through distributed shared
+// memory (two cluster barriers per step, double-buffered slots).
+// Larger n (cpqr_small_kernel): one CTA of 1024 threads works in place on a
+// copy of W held row-major in global memory (L2-resident); thread t owns
+// columns t, t + 1024, ...
+// In both, norms and the argmax use warp shuffles and fixed-order sums, and
+// the reflector of the pivot column is formed by one warp.
+#include <cooperative_groups.h>
 #include <float.h>
 
 #include "idsk_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace idsk {
 namespace {
@@ -100,7 +111,7 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
         const double x = M[(int64_t)i * ld + j];
         ss += x * x;
       }
-      best = better(best, ArgMax{sqrt(ss), j});
+      best = better(best, ArgMax{ss, j});
     }
     best = warp_argmax(best);
     if (lane == 0) red[warp] = best;
@@ -110,7 +121,7 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
       b = warp_argmax(b);
       if (lane == 0) {
         sh_p = b.i;
-        sh_stop = !(b.v > sh_tol);
+        sh_stop = !(b.v > sh_tol * sh_tol);
       }
     }
     __syncthreads();
@@ -168,12 +179,150 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
   for (int q = s + t; q < k; q += NT) J[q] = -1;
 }
 
+constexpr int CL_CTAS = 8, CL_THREADS = 128;   // cluster kernel: n <= 1024
+
+__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
+    cpqr_cluster_kernel(const double* __restrict__ M, int rows, int n, int ld, int k,
+                        double tol_factor, double* __restrict__ R, int* __restrict__ J,
+                        int* __restrict__ colpos, int* __restrict__ kout) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ ArgMax cand[2];              // this CTA's best candidate (by step parity)
+  __shared__ double pcol[2][kLMax];       // pivot column, published by its owner CTA
+  __shared__ double fro_cta;
+  __shared__ ArgMax wred[CL_THREADS / 32];
+  __shared__ double fred[CL_THREADS / 32];
+  __shared__ double vs[kLMax];
+  __shared__ double sh_tau, sh_beta;
+  const int rank = (int)cl.block_rank();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int j = rank * CL_THREADS + t;
+  const bool have = j < n;
+  const int kmax = min(k, min(rows, n));
+  double c[kLMax];
+#pragma unroll
+  for (int i = 0; i < kLMax; ++i) c[i] = (have && i < rows) ? M[(int64_t)i * ld + j] : 0.0;
+  if (have) colpos[j] = -1;
+  bool piv = false;
+
+  // ||W||_F: rows in order per column, then warps, then CTAs in rank order
+  {
+    double ss = 0.0;
+#pragma unroll
+    for (int i = 0; i < kLMax; ++i) ss += c[i] * c[i];
+    ss = warp_sum(ss);
+    if (lane == 0) fred[warp] = ss;
+    __syncthreads();
+    if (t == 0) {
+      double a = 0.0;
+      for (int w = 0; w < CL_THREADS / 32; ++w) a += fred[w];
+      fro_cta = a;
+    }
+  }
+  cl.sync();
+  double fro2 = 0.0;
+  for (int r = 0; r < CL_CTAS; ++r) fro2 += *cl.map_shared_rank(&fro_cta, r);
+  const double tol = tol_factor * DBL_EPSILON * sqrt(fro2);
+
+  int s = 0;
+  for (; s < kmax; ++s) {
+    const int b = s & 1;
+    // residual norm of this thread's column, rows s.. in order
+    ArgMax best{-1.0, 0x7fffffff};
+    if (have && !piv) {
+      double ss = 0.0;
+#pragma unroll
+      for (int i = 0; i < kLMax; ++i)
+        if (i >= s && i < rows) ss += c[i] * c[i];
+      best = ArgMax{ss, j};
+    }
+    best = warp_argmax(best);
+    if (lane == 0) wred[warp] = best;
+    __syncthreads();
+    if (t == 0) {
+      ArgMax a = wred[0];
+      for (int w = 1; w < CL_THREADS / 32; ++w) a = better(a, wred[w]);
+      cand[b] = a;
+    }
+    cl.sync();   // candidates published
+    ArgMax g = *cl.map_shared_rank(&cand[b], 0);
+    for (int r = 1; r < CL_CTAS; ++r) g = better(g, *cl.map_shared_rank(&cand[b], r));
+    if (!(g.v > tol * tol)) break;   // uniform over the cluster
+    const int p = g.i;
+    if (j == p) {
+#pragma unroll
+      for (int i = 0; i < kLMax; ++i) pcol[b][i] = c[i];
+    }
+    cl.sync();   // pivot column published
+    if (warp == 0) {   // Householder reflector of the pivot column, rows s..rows-1
+      const double* pc = cl.map_shared_rank(&pcol[b][0], p / CL_THREADS);
+      const int len = rows - s;
+      const double x0 = (lane < len) ? pc[s + lane] : 0.0;
+      const double x1 = (lane + 32 < len) ? pc[s + lane + 32] : 0.0;
+      const double alpha = __shfl_sync(0xffffffffu, x0, 0);
+      const double sigma = warp_sum((lane == 0 ? 0.0 : x0 * x0) + x1 * x1);
+      double tau = 0.0, beta = alpha, scale = 0.0;
+      if (sigma != 0.0) {
+        const double nrm = sqrt(alpha * alpha + sigma);
+        beta = alpha >= 0.0 ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = alpha - beta;
+      }
+      if (lane < len) vs[lane] = lane == 0 ? 1.0 : (sigma != 0.0 ? x0 / scale : 0.0);
+      if (lane + 32 < len) vs[lane + 32] = sigma != 0.0 ? x1 / scale : 0.0;
+      if (lane == 0) {
+        sh_tau = tau;
+        sh_beta = beta;
+        if (rank == 0) {
+          J[s] = p;
+          colpos[p] = s;
+        }
+      }
+    }
+    __syncthreads();
+    if (have) {
+      double rsj;
+      if (j == p) {
+        piv = true;
+        rsj = sh_beta;
+      } else if (piv) {
+        rsj = 0.0;
+      } else {
+        const double tau = sh_tau;
+        if (tau != 0.0) {
+          double d = 0.0;
+#pragma unroll
+          for (int i = 0; i < kLMax; ++i)
+            if (i >= s && i < rows) d += vs[i - s] * c[i];
+          const double td = tau * d;
+#pragma unroll
+          for (int i = 0; i < kLMax; ++i)
+            if (i >= s && i < rows) c[i] -= td * vs[i - s];
+        }
+#pragma unroll
+        for (int i = 0; i < kLMax; ++i)
+          if (i == s) rsj = c[i];
+      }
+      R[(int64_t)s * n + j] = rsj;
+    }
+  }
+  if (rank == 0) {
+    if (t == 0) *kout = s;
+    for (int q = s + t; q < k; q += CL_THREADS) J[q] = -1;
+  }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 // P(:, j) for every column j: e_u when j = J[u]; otherwise the solution of
-// R11 x = R(:, j) by back-substitution, R11(t, u) = R(t, J[u]).
-__global__ void solve_p_kernel(const double* __restrict__ R, const int* __restrict__ J,
-                               const int* __restrict__ colpos, const int* __restrict__ kout,
-                               int k, int n, double* __restrict__ P) {
-  extern __shared__ double r11[];   // kk x kk
+// R11 x = R(:, j) by back-substitution, R11(t, u) = R(t, J[u]).  R11 and the
+// solution vectors of the block's columns live in shared memory.
+constexpr int SP_THREADS = 64;
+constexpr int SP_LD = kLMax + 1;   // odd stride: per-thread rows on distinct banks
+__global__ void __launch_bounds__(SP_THREADS) solve_p_kernel(
+    const double* __restrict__ R, const int* __restrict__ J, const int* __restrict__ colpos,
+    const int* __restrict__ kout, int k, int n, double* __restrict__ P) {
+  extern __shared__ double sm[];
+  double* xs = sm;                              // [SP_THREADS][SP_LD]
+  double* r11 = sm + SP_THREADS * SP_LD;        // kk x kk
   __shared__ int Js[kLMax];
   const int kk = *kout;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) Js[e] = J[e];
@@ -190,12 +339,13 @@ __global__ void solve_p_kernel(const double* __restrict__ R, const int* __restri
     for (int tt = 0; tt < k; ++tt) P[(int64_t)tt * n + j] = (tt == cp) ? 1.0 : 0.0;
     return;
   }
-  for (int tt = kk; tt < k; ++tt) P[(int64_t)tt * n + j] = 0.0;
+  double* x = xs + threadIdx.x * SP_LD;
   for (int tt = kk - 1; tt >= 0; --tt) {
-    double x = R[(int64_t)tt * n + j];
-    for (int u = tt + 1; u < kk; ++u) x -= r11[tt * kk + u] * P[(int64_t)u * n + j];
-    P[(int64_t)tt * n + j] = x / r11[tt * kk + tt];
+    double v = R[(int64_t)tt * n + j];
+    for (int u = tt + 1; u < kk; ++u) v -= r11[tt * kk + u] * x[u];
+    x[tt] = v / r11[tt * kk + tt];
   }
+  for (int tt = 0; tt < k; ++tt) P[(int64_t)tt * n + j] = tt < kk ? x[tt] : 0.0;
 }
 
 }  // namespace
@@ -203,21 +353,25 @@ __global__ void solve_p_kernel(const double* __restrict__ R, const int* __restri
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
                               double* R, int* J, int* colpos, int* kout, cudaStream_t st) {
   if (n > NT * QMAX || rows > kLMax) return cudaErrorInvalidValue;
-  cpqr_small_kernel<<<1, NT, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J, colpos, kout);
+  if (n <= CL_CTAS * CL_THREADS)
+    cpqr_cluster_kernel<<<CL_CTAS, CL_THREADS, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J,
+                                                        colpos, kout);
+  else
+    cpqr_small_kernel<<<1, NT, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J, colpos, kout);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
                            int k, int n, double* P, cudaStream_t st) {
-  const int nt = 256;
-  const size_t sm = sizeof(double) * (size_t)k * k;
+  const size_t sm = sizeof(double) * ((size_t)SP_THREADS * SP_LD + (size_t)k * k);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(solve_p_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  solve_p_kernel<<<(n + nt - 1) / nt, nt, sm, st>>>(R, J, colpos, kout, k, n, P);
+  solve_p_kernel<<<(n + SP_THREADS - 1) / SP_THREADS, SP_THREADS, sm, st>>>(R, J, colpos, kout,
+                                                                           k, n, P);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -104,6 +104,7 @@ struct SketchArgs {
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
   double* wpart;        // tensor-core kernel: per-CTA FP64 W^T slabs [nsm][64][512]
+  int32_t prefetch;     // tensor-core kernel: tiles of A prefetched into L2 ahead of use
 };
 
 }  // namespace idsk
@@ -133,6 +134,7 @@ struct id_sketch {
   bool poisoned = false;
   int sketch_kernel = 0;         // 0 auto, 1 tensor cores, 2 SIMT (IDSKETCH_SKETCH)
   int drain_blocks = 8;          // row blocks between FP64 flushes of W^T (tensor cores)
+  int prefetch_tiles = 3;        // tiles of A prefetched into L2 ahead (tensor cores)
   int* d_status = nullptr;       // nonzero: a bounded device wait gave up
   double* d_wpart = nullptr;     // per-CTA W^T slabs of the tensor-core sketch
 
@@ -148,13 +150,13 @@ struct id_sketch {
   double* d_F = nullptr;      // n_max x k
   double* d_nu2 = nullptr;    // n_max
   double* d_nu20 = nullptr;   // n_max
-  double* d_gvec = nullptr;   // n_max: A_c^T v_s
+  double* d_gvec = nullptr;   // coarse_blocks x n_max: row-range partials of A_c^T u
   double* d_hvec = nullptr;   // kLMax: V_s^T v_s
-  float* d_vh = nullptr;      // mc: v_s as an FP32 pair (hi)
+  float* d_vh = nullptr;      // mc: u below row s as an FP32 pair (hi)
   float* d_vl = nullptr;      // mc: (lo)
-  double* d_upart = nullptr;  // coarse_blocks
+  double* d_upart = nullptr;  // coarse_blocks x (kLMax + 1): partials of V_s^T u, ||u||^2
   double* d_cscal = nullptr;  // 8 scalars
-  int* d_cint = nullptr;      // 4 ints: pivot, stop, nrecompute, k_out
+  int* d_cint = nullptr;      // 8 ints: pivot, stop, nrecompute, k_out, 2 CTA counters
   int* d_rlist = nullptr;     // n_max
   double* d_Rc = nullptr;     // k x n_max
   double* d_Pc = nullptr;     // k x n_max

@@ -88,7 +88,7 @@ enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE
        NBAR = B_RE0 + NST };
 
 struct Smem {
-  uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES] (TMA form: one buffer)
+  uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES] (TMA form: [2 slots][PIECE_BYTES])
   uint32_t raw;      // TMA form: [NST][RAW_BYTES]
   uint32_t rc;       // TMA form: coarse index of the 128 rows of the row block
   uint32_t omega;    // [kTcMaxTiles][OMEGA_TILE_BYTES]
@@ -111,6 +111,34 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, 
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(tmap), "r"(x), "r"(y), "r"(bar)
       : "memory");
+}
+
+// L2 prefetch of one box of the tensor map (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(uint64_t tmap, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
+// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned address.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// Named barrier 1 over the converter warps that also ORs a predicate.
+__device__ __forceinline__ bool conv_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(NCONV * 32)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
@@ -156,7 +184,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   Smem S;
   S.pieces = base;
-  S.omega = S.pieces + (TMA ? 1u : 2u) * NP * PIECE_BYTES;
+  S.omega = S.pieces + (TMA ? 2u : 2u * NP) * PIECE_BYTES;
   S.psi = S.omega + kTcMaxTiles * OMEGA_TILE_BYTES;
   S.raw = S.psi + 2u * PSI_BYTES;
   S.rc = S.raw + (TMA ? NST * RAW_BYTES : 0u);
@@ -190,7 +218,6 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     mbar_init(bar(B_WE), NEPI);
     mbar_init(bar(B_DONE), 1);
     if (TMA) {
-      mbar_init(bar(B_FULL0), NCONV);   // one piece buffer: FULL0/FREE0 only
       for (int st = 0; st < NST; ++st) {
         mbar_init(bar(B_RF0 + st), 1);
         mbar_init(bar(B_RE0 + st), NCONV);
@@ -228,9 +255,13 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     if constexpr (TMA) {
     // ------------------------------------------------------ converters (TMA)
     // Raw FP32 boxes (32 columns x 128 rows, 512 B per column) arrive in an
-    // NST-stage ring; thread (warp w, lane l) splits column 4w + l/8, rows
-    // 4(l%8) + 32g of each box into the (single) piece buffer.
-    const int cl = warp * 4 + (lane >> 3);
+    // NST-stage ring; thread (warp w, lane l) splits one column, rows
+    // 4(l%8) + 32g of each box into the (single) piece buffer.  The eight
+    // lanes of a quarter warp share a column; the two quarters of each half
+    // warp take columns 4 apart, so that every 8-byte store phase covers all
+    // 32 banks of the 128-byte-swizzled piece (columns c and c + 4 have
+    // disjoint 16-byte chunk positions for rows 0-31).
+    const int cl = (warp >> 1) * 8 + (warp & 1) * 2 + ((lane >> 3) & 1) * 4 + (lane >> 4);
     const int rq = (lane & 7) * 4;
     int64_t* rcs = reinterpret_cast<int64_t*>(smem_raw + (S.rc - smem_u32(smem_raw)));
     const uint8_t* rawp = smem_raw + (S.raw - smem_u32(smem_raw));
@@ -238,22 +269,34 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
       const int64_t rbase = (rb_begin + i) * TR;
+      // coarse-grid rows of this row block (most row blocks hold none)
+      bool gather = false;
       if (a.cg.on) {
         asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
-        if (tid < TR) rcs[tid] = (rbase + tid < a.m) ? coarse_index_tc(rbase + tid, a.cg) : -1;
-        asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
+        int64_t rcv = -1;
+        if (tid < TR) {
+          rcv = (rbase + tid < a.m) ? coarse_index_tc(rbase + tid, a.cg) : -1;
+          rcs[tid] = rcv;
+        }
+        gather = conv_bar_or(rcv >= 0);
       }
       for (int ct = 0; ct < nct && ok; ++ct, ++t) {
-        if (t >= 1 && !mbar_wait(bar(B_FREE0), (t - 1) & 1, S.abort_flag)) {
+        // Piece units u = NP t + p take the two piece slots in turn (slot
+        // u & 1, its (u >> 1)-th use): with NP = 2 the MMAs of one piece run
+        // while the converters write the other.
+        const int u0 = NP * t, s0 = u0 & 1;
+        if ((u0 >> 1) >= 1 &&
+            !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag)) {
           ok = false;
           break;
         }
+        const uint32_t hi_buf = S.pieces + (uint32_t)s0 * PIECE_BYTES;
+        uint32_t lo_keep[NP > 1 ? 32 : 1];   // second piece, packed, until its slot frees
+#pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int u = 4 * t + j, st = u % NST;
-          if (!mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) {
-            ok = false;
-            break;
-          }
+          if (ok && !mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) ok = false;
+          if (!ok) continue;
           const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
           const int cc = 32 * j + cl;              // column inside the tile
           const int wc = ct * TCOLS + cc;          // column inside the window
@@ -263,16 +306,16 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             const float4 x = *reinterpret_cast<const float4*>(raw + cl * TR + rr);
             const uint32_t off = swz((uint32_t)cc, (uint32_t)rr, 2048u);
             const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
-            st_shared_v2(S.pieces + off, h01, h23);
+            st_shared_v2(hi_buf + off, h01, h23);
             if (NP > 1) {
               const float2 f01 =
                   __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h01));
               const float2 f23 =
                   __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h23));
-              st_shared_v2(S.pieces + PIECE_BYTES + off, pack_bf16x2(x.x - f01.x, x.y - f01.y),
-                           pack_bf16x2(x.z - f23.x, x.w - f23.y));
+              lo_keep[(j * 4 + g) * 2] = pack_bf16x2(x.x - f01.x, x.y - f01.y);
+              lo_keep[(j * 4 + g) * 2 + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
             }
-            if (a.cg.on && wc < w.ncols) {
+            if (gather && wc < w.ncols) {
               float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc);
               const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -288,7 +331,25 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         if (!ok) break;
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_FULL0));
+        if (lane == 0) mbar_arrive(bar(B_FULL0 + s0));
+        if (NP > 1) {
+          const int u1 = u0 + 1;   // slot 1
+          if ((u1 >> 1) >= 1 &&
+              !mbar_wait(bar(B_FREE1), ((u1 >> 1) - 1) & 1, S.abort_flag)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+              st_shared_v2(S.pieces + PIECE_BYTES +
+                               swz((uint32_t)(32 * j + cl), (uint32_t)(32 * g + rq), 2048u),
+                           lo_keep[(j * 4 + g) * 2], lo_keep[(j * 4 + g) * 2 + 1]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_FULL1));
+        }
         if (warp == 0 && lane == 0) TC_TRACE(0, t);
       }
     }
@@ -351,6 +412,18 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       }
       for (int ct = 0; ct < nct; ++ct, ++t) {
         const int cbase = ct * TCOLS;
+        if (a.prefetch > 0 && tid < TCOLS && t + a.prefetch < ntile) {
+          // column tid of tile t + prefetch into L2
+          const int tt = t + a.prefetch;
+          const int i2 = tt / nct;
+          const int c = (tt - i2 * nct) * TCOLS + tid;
+          const int64_t rp = (rb_begin + i2) * TR;
+          const int64_t rows = a.m - rp < TR ? a.m - rp : TR;
+          const uint32_t bytes = (uint32_t)(rows * 4) & ~15u;
+          if (c < w.ncols && bytes > 0)
+            bulk_prefetch_l2(one_seg ? seg_base + (int64_t)c * seg_ld + rp : column_ptr(w, c) + rp,
+                             bytes);
+        }
         load_half(r0, cbase + c_hi, bufB);                       // half 1 of this tile
         const int b = t & 1;
         if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) {
@@ -434,8 +507,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       if (drain_due(i)) {
         if (!mbar_wait(bar(B_WF), wd & 1, S.abort_flag, 256)) break;
         tc_fence_after();
-        // W^T partials -> this CTA's private FP64 slab wpart[cta][s][c]
-        // (plain read-modify-write; the first flush of the launch stores)
+        // W^T partials -> this CTA's private FP64 slab wpart[cta][s][c]: the
+        // first flush of the launch stores, later ones add in L2.  Each slab
+        // entry is written by one thread only, in program order, so the sum is
+        // taken in a fixed order.
         double* slab = a.wpart + (int64_t)blockIdx.x * LP * (kTcMaxTiles * TCOLS);
         for (int ct = 0; ct < nct; ++ct) {
           const int c = ct * TCOLS + rl;
@@ -448,12 +523,9 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
 #pragma unroll
               for (int j = 0; j < 32; ++j) dst[(int64_t)j * (kTcMaxTiles * TCOLS)] = (double)v[j];
             } else {
-              double old[32];
-#pragma unroll
-              for (int j = 0; j < 32; ++j) old[j] = dst[(int64_t)j * (kTcMaxTiles * TCOLS)];
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                dst[(int64_t)j * (kTcMaxTiles * TCOLS)] = old[j] + (double)v[j];
+                red_add_f64(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j]);
             }
           }
         }
@@ -483,8 +555,8 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       const uint32_t psi_s = S.psi + (uint32_t)pb * PSI_BYTES;
       const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + pb * LP);
       for (int ct = 0; ct < nct; ++ct, ++t) {
-        const int b = TMA ? 0 : (t & 1);
-        if (!mbar_wait(bar(B_FULL0 + b), TMA ? (t & 1) : ((t >> 1) & 1), S.abort_flag)) {
+        const int b = t & 1;
+        if (!TMA && !mbar_wait(bar(B_FULL0 + b), (t >> 1) & 1, S.abort_flag)) {
           ok = false;
           break;
         }
@@ -495,7 +567,16 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         const uint32_t om = S.omega + (uint32_t)ct * OMEGA_TILE_BYTES;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const uint32_t pa = pbuf + (uint32_t)p * PIECE_BYTES;
+          uint32_t pa = pbuf + (uint32_t)p * PIECE_BYTES;
+          const int u = NP * t + p;   // TMA form: piece unit u in slot u & 1
+          if (TMA) {
+            if (!mbar_wait(bar(B_FULL0 + (u & 1)), (u >> 1) & 1, S.abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            pa = S.pieces + (uint32_t)(u & 1) * PIECE_BYTES;
+          }
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {   // W^T: K = 16 rows per instruction
             const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
@@ -510,9 +591,11 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             mma_bf16(ytm, sdesc(pa + (uint32_t)kk * 4096u, 1024u, 2048u),
                      sdesc(om + ko, 0u, 2048u), IDESC_Y, acc);
           }
+          if (TMA) mma_commit(bar(B_FREE0 + (u & 1)));
         }
+        if (!ok) break;
         accw |= 1u << ct;
-        mma_commit(bar(B_FREE0 + b));
+        if (!TMA) mma_commit(bar(B_FREE0 + b));
       }
       if (!ok) break;
       mma_commit(bar(B_YF0 + pb));
@@ -552,6 +635,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES, tm, row, ct * TCOLS + 32 * j,
                     bar(B_RF0 + st));
       }
+      if (ok && a.prefetch > 0 && t + a.prefetch < ntile) {   // tile t + prefetch into L2
+        const int tt = t + a.prefetch;
+        const int i2 = tt / nct, ct2 = tt - i2 * nct;
+        for (int j = 0; j < 4; ++j)
+          tma_prefetch_2d(tm, (int)((rb_begin + i2) * TR), ct2 * TCOLS + 32 * j);
+      }
     }
   }
   tc_fence_before();
@@ -583,7 +672,7 @@ __global__ void wpart_reduce_kernel(const double* __restrict__ wpart, int nslab,
 
 template <int NP, bool TMA>
 size_t tc_smem_bytes() {
-  return 1024 + (TMA ? 1u : 2u) * NP * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES +
+  return 1024 + (TMA ? 2u : 2u * NP) * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES +
          2u * PSI_BYTES + (TMA ? NST * RAW_BYTES + TR * 8u : 0u) + NBAR * 8 + 16;
 }
 

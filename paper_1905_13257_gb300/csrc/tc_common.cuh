@@ -63,6 +63,22 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_f
   }
 }
 
+// Bounded wait without sleeping between polls (try_wait itself suspends the
+// thread for a while): for waits on the critical path of a streaming loop.
+__device__ inline bool mbar_wait_spin(uint32_t bar, uint32_t parity, uint32_t abort_flag) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      if (ld_volatile_shared(abort_flag)) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        st_volatile_shared(abort_flag, 1);
+        return false;
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
