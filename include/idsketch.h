@@ -186,6 +186,18 @@ id_status id_sketch_get(id_sketch* h, const double** d_W, const void** d_Y, cons
 /* Release every device buffer of the handle (synchronises its stream). */
 void id_sketch_destroy(id_sketch* h);
 
+/* Kernel timing, a measurement aid with no counterpart in the paper.
+ * id_timing_enable(h, 1) makes the handle record CUDA events on its stream
+ * around every launch of the fused tensor-core sketch kernel (which = 0) and
+ * of the error-pass kernel (which = 1); id_timing_enable(h, 0) stops and
+ * frees them.  id_timing_read waits for the last recorded launch of that
+ * kernel, returns the summed launch durations (ms) and the number of
+ * launches since the previous read, and starts a new accumulation.
+ * Errors: ID_ERR_INVALID_ARG (bad which / NULL output), ID_ERR_STATE (timing
+ * not enabled), ID_ERR_CUDA. */
+id_status id_timing_enable(id_sketch* h, int32_t on);
+id_status id_timing_read(id_sketch* h, int32_t which, double* total_ms, int64_t* launches);
+
 /* Fill out[(i - first) * width + s] = G(i, s) for i in [first, first+count),
  * s in [0, width): the same counter-based Gaussian entries the sketch uses,
  * which = 1 for Psi (G(i,s) = Psi[s, i]) and which = 2 for Omega

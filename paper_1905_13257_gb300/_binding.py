@@ -66,6 +66,9 @@ SIGNATURES = {
                                 C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "id_sketch_destroy": (None, [C.c_void_p]),
+    "id_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "id_timing_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_int64)]),
     "id_gaussian_fill": (C.c_int, [C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_int32,
                                    C.c_void_p, C.c_void_p]),
     "id_gaussian_table": (C.c_int, [C.POINTER(C.c_uint16)]),

@@ -96,6 +96,18 @@ class IdSketch:
         B.check(self.lib.id_sketch_reset(self.h), "id_sketch_reset")
         self._keep = []
 
+    def timing(self, on=True):
+        """Record CUDA events around each launch of the fused sketch kernel and
+        of the error-pass kernel (id_timing_enable)."""
+        B.check(self.lib.id_timing_enable(self.h, 1 if on else 0), "id_timing_enable")
+
+    def read_timing(self, which):
+        """(total ms, launches) of 'sketch' or 'recon' since the last read."""
+        ms, cnt = C.c_double(), C.c_int64()
+        B.check(self.lib.id_timing_read(self.h, {"sketch": 0, "recon": 1}[which], C.byref(ms),
+                                        C.byref(cnt)), "id_timing_read")
+        return ms.value, cnt.value
+
     def n_seen(self):
         n = C.c_int64()
         B.check(self.lib.id_sketch_get(self.h, None, None, None, C.byref(n), None), "id_sketch_get")

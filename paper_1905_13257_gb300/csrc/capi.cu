@@ -180,10 +180,9 @@ id_status launch_pending(id_sketch* h) {
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
     a.wpart = h->d_wpart;
-    a.prefetch = h->prefetch_tiles;
     if (tc) {
       IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, h->nsm, h->drain_blocks, h->d_status,
-                                    h->st));
+                                    h->st, h->timer_sketch));
     } else {
       IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, h->nsm, h->st));
     }
@@ -293,7 +292,6 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
     if (!strcmp(e, "simt")) h->sketch_kernel = 2;
   }
   if (const char* e = getenv("IDSKETCH_DRAIN_BLOCKS")) h->drain_blocks = std::max(1, atoi(e));
-  if (const char* e = getenv("IDSKETCH_PREFETCH_TILES")) h->prefetch_tiles = std::max(0, atoi(e));
   const int64_t nm = h->n_max;
   const int k = h->k, l = h->l;
   Allocator al;
@@ -474,7 +472,8 @@ id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64
   IDSK_CUDA(h, cudaMemcpyAsync(h->d_Jin, jh, sizeof(int32_t) * k, cudaMemcpyHostToDevice, h->st));
   IDSK_CUDA(h, cudaMemcpyAsync(h->d_Pin, P, sizeof(double) * k * n, cudaMemcpyDefault, h->st));
   IDSK_CUDA(h, launch_recon_error(d_A, lda, h->m, n, h->cfg.dtype, h->d_Jin, h->d_Pin, k,
-                                  h->d_part, h->rec_blocks, h->d_out3, h->d_status, h->st));
+                                  h->d_part, h->rec_blocks, h->d_out3, h->d_status, h->st,
+                                  h->timer_recon));
   double o[3];
   int32_t dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(o, h->d_out3, sizeof(o), cudaMemcpyDeviceToHost, h->st));
@@ -503,10 +502,34 @@ id_status id_sketch_get(id_sketch* h, const double** d_W, const void** d_Y, cons
   return ID_OK;
 }
 
+id_status id_timing_enable(id_sketch* h, int32_t on) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (on) {
+    if (!h->timer_sketch) h->timer_sketch = new idsk::KernelTimer();
+    if (!h->timer_recon) h->timer_recon = new idsk::KernelTimer();
+  } else {
+    cudaStreamSynchronize(h->st);
+    delete h->timer_sketch;
+    delete h->timer_recon;
+    h->timer_sketch = h->timer_recon = nullptr;
+  }
+  return ID_OK;
+}
+
+id_status id_timing_read(id_sketch* h, int32_t which, double* total_ms, int64_t* launches) {
+  if (!h || (which != 0 && which != 1) || !total_ms || !launches) return ID_ERR_INVALID_ARG;
+  idsk::KernelTimer* t = which == 0 ? h->timer_sketch : h->timer_recon;
+  if (!t) return ID_ERR_STATE;
+  IDSK_CUDA(h, t->read(total_ms, launches));
+  return ID_OK;
+}
+
 void id_sketch_destroy(id_sketch* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   free_all(h);
+  delete h->timer_sketch;
+  delete h->timer_recon;
   delete h;
 }
 

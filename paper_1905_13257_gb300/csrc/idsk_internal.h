@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include <vector>
+
 #include "idsketch.h"
 
 namespace idsk {
@@ -104,7 +106,45 @@ struct SketchArgs {
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
   double* wpart;        // tensor-core kernel: per-CTA FP64 W^T slabs [nsm][64][512]
-  int32_t prefetch;     // tensor-core kernel: tiles of A prefetched into L2 ahead of use
+};
+
+// CUDA events recorded around the main kernel of a launcher, on the launching
+// stream (optional measurement; the launchers take a null pointer when off).
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;   // start, stop, start, stop, ...
+  size_t used = 0;               // events recorded since the last read
+  cudaError_t mark(cudaStream_t st) {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      const cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+    }
+    return cudaEventRecord(ev[used++], st);
+  }
+  // Sum of the recorded (stop - start) intervals in ms; waits for the last
+  // event and starts a new accumulation.
+  cudaError_t read(double* ms, int64_t* pairs) {
+    double tot = 0.0;
+    const size_t np = used / 2;
+    if (np > 0) {
+      cudaError_t r = cudaEventSynchronize(ev[2 * np - 1]);
+      if (r != cudaSuccess) return r;
+      for (size_t q = 0; q < np; ++q) {
+        float t = 0.f;
+        r = cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]);
+        if (r != cudaSuccess) return r;
+        tot += t;
+      }
+    }
+    used = 0;
+    *ms = tot;
+    *pairs = (int64_t)np;
+    return cudaSuccess;
+  }
+  ~KernelTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 }  // namespace idsk
@@ -134,7 +174,6 @@ struct id_sketch {
   bool poisoned = false;
   int sketch_kernel = 0;         // 0 auto, 1 tensor cores, 2 SIMT (IDSKETCH_SKETCH)
   int drain_blocks = 8;          // row blocks between FP64 flushes of W^T (tensor cores)
-  int prefetch_tiles = 3;        // tiles of A prefetched into L2 ahead (tensor cores)
   int* d_status = nullptr;       // nonzero: a bounded device wait gave up
   double* d_wpart = nullptr;     // per-CTA W^T slabs of the tensor-core sketch
 
@@ -170,6 +209,10 @@ struct id_sketch {
   double* d_Pin = nullptr;    // kRecKMax x pin_cap
   int64_t pin_cap = 0;
   int rec_blocks = 0;
+  // id_timing_enable: events around the fused sketch kernel and the error-pass
+  // kernel
+  idsk::KernelTimer* timer_sketch = nullptr;
+  idsk::KernelTimer* timer_recon = nullptr;
 };
 
 // ------------------------------------------------------------- launchers
@@ -180,7 +223,8 @@ cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64
 cudaError_t launch_sketch_simt(const SketchArgs& a, const Window& w, int dtype, int nsm,
                                cudaStream_t st);
 cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
-                             int drain_blocks, int* status, cudaStream_t st);
+                             int drain_blocks, int* status, cudaStream_t st,
+                             KernelTimer* timer = nullptr);
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
                               double* R, int* J, int* colpos, int* kout, cudaStream_t st);
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
@@ -188,11 +232,12 @@ cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, con
 cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
-                               double* out3, int* status, cudaStream_t st);
+                               double* out3, int* status, cudaStream_t st,
+                               KernelTimer* timer = nullptr);
 int recon_tc_grid(int64_t m, int64_t n, int nsm);
 cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
                             const double* P, int k, double* part, int grid, int* status,
-                            cudaStream_t st);
+                            cudaStream_t st, KernelTimer* timer = nullptr);
 void gaussian_table_host(float* vals, uint16_t* bits);
 void count_launches(int64_t n);
 }  // namespace idsk

@@ -149,7 +149,7 @@ size_t recon_smem(void) {
 
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
-                               double* out3, int* status, cudaStream_t st) {
+                               double* out3, int* status, cudaStream_t st, KernelTimer* timer) {
   cudaError_t e;
   if (dtype == ID_F32 && m >= 128) {
     // FP32 data: tensor-core pass (products split into bf16 pieces)
@@ -160,7 +160,7 @@ cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n,
     const int grid = std::min(recon_tc_grid(m, n, nsm), nblk);
     if (grid * 1 < (int)((n + 255) / 256)) return cudaErrorInvalidValue;
     e = launch_recon_tc(reinterpret_cast<const float*>(A), lda, m, n, J, P, k, part, grid,
-                        status, st);
+                        status, st, timer);
     if (e != cudaSuccess) return e;
     recon_finalize_kernel<<<1, 32, 0, st>>>(part, grid, out3);
     count_launches(1);
@@ -168,6 +168,7 @@ cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n,
   }
   const int64_t ntiles = (m + TM - 1) / TM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, nblk));
+  if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
   if (dtype == ID_F64) {
     const size_t sm = recon_smem<double>();
     e = cudaFuncSetAttribute(recon_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -185,6 +186,7 @@ cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n,
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
   recon_finalize_kernel<<<1, 32, 0, st>>>(part, grid, out3);
   count_launches(2);
   return cudaGetLastError();

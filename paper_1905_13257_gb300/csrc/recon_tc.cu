@@ -342,14 +342,17 @@ int recon_tc_grid(int64_t m, int64_t n, int nsm) {
 
 cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
                             const double* P, int k, double* part, int grid, int* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, KernelTimer* timer) {
   const size_t sm = 1024 + 3u * P_PIECE + 6u * S_PIECE + NBAR * 8 + 16;
   cudaError_t e = cudaFuncSetAttribute(recon_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
   recon_tc_kernel<<<grid, NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status);
   count_launches(1);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (timer) e = timer->mark(st);
+  return e;
 }
 
 }  // namespace idsk

@@ -103,30 +103,36 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
+// L2 policies: A streams through once (evict first); the per-CTA W^T slabs
+// are read-modify-written every few row blocks and should stay in L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 // 2D tiled TMA load of one box (x = row, y = column) into shared memory.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, int y,
-                                            uint32_t bar) {
+                                            uint32_t bar, uint64_t policy) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(tmap), "r"(x), "r"(y), "r"(bar)
+      ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
 }
 
-// L2 prefetch of one box of the tensor map (no shared memory, no completion).
-__device__ __forceinline__ void tma_prefetch_2d(uint64_t tmap, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap),
-               "r"(x), "r"(y)
+__device__ __forceinline__ void st_f64_hint(double* p, double v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
                : "memory");
 }
-
-// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned address.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void red_add_f64(double* p, double v) {
-  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+__device__ __forceinline__ void red_add_f64(double* p, double v, uint64_t policy) {
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
+               : "memory");
 }
 
 // Named barrier 1 over the converter warps that also ORs a predicate.
@@ -412,18 +418,6 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       }
       for (int ct = 0; ct < nct; ++ct, ++t) {
         const int cbase = ct * TCOLS;
-        if (a.prefetch > 0 && tid < TCOLS && t + a.prefetch < ntile) {
-          // column tid of tile t + prefetch into L2
-          const int tt = t + a.prefetch;
-          const int i2 = tt / nct;
-          const int c = (tt - i2 * nct) * TCOLS + tid;
-          const int64_t rp = (rb_begin + i2) * TR;
-          const int64_t rows = a.m - rp < TR ? a.m - rp : TR;
-          const uint32_t bytes = (uint32_t)(rows * 4) & ~15u;
-          if (c < w.ncols && bytes > 0)
-            bulk_prefetch_l2(one_seg ? seg_base + (int64_t)c * seg_ld + rp : column_ptr(w, c) + rp,
-                             bytes);
-        }
         load_half(r0, cbase + c_hi, bufB);                       // half 1 of this tile
         const int b = t & 1;
         if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) {
@@ -512,6 +506,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         // entry is written by one thread only, in program order, so the sum is
         // taken in a fixed order.
         double* slab = a.wpart + (int64_t)blockIdx.x * LP * (kTcMaxTiles * TCOLS);
+        const uint64_t keep = policy_evict_last();
         for (int ct = 0; ct < nct; ++ct) {
           const int c = ct * TCOLS + rl;
 #pragma unroll
@@ -521,11 +516,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             double* dst = slab + (int64_t)(h * 32) * (kTcMaxTiles * TCOLS) + c;
             if (wd == 0) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) dst[(int64_t)j * (kTcMaxTiles * TCOLS)] = (double)v[j];
+              for (int j = 0; j < 32; ++j)
+                st_f64_hint(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j], keep);
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                red_add_f64(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j]);
+                red_add_f64(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j], keep);
             }
           }
         }
@@ -620,6 +616,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   } else if (TMA && warp == PROD_WARP && lane == 0) {
     // -------------------------------------------------------- TMA producer
     const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
+    const uint64_t stream_once = policy_evict_first();
     int u = 0;
     bool ok = true;
     for (int t = 0; t < ntile && ok; ++t) {
@@ -633,13 +630,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         }
         mbar_expect_tx(bar(B_RF0 + st), RAW_BYTES);
         tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES, tm, row, ct * TCOLS + 32 * j,
-                    bar(B_RF0 + st));
-      }
-      if (ok && a.prefetch > 0 && t + a.prefetch < ntile) {   // tile t + prefetch into L2
-        const int tt = t + a.prefetch;
-        const int i2 = tt / nct, ct2 = tt - i2 * nct;
-        for (int j = 0; j < 4; ++j)
-          tma_prefetch_2d(tm, (int)((rb_begin + i2) * TR), ct2 * TCOLS + 32 * j);
+                    bar(B_RF0 + st), stream_once);
       }
     }
   }
@@ -720,20 +711,24 @@ bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
 
 template <int NP, bool TMA>
 cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int drain_blocks,
-                           int* status, const CUtensorMap& tm, cudaStream_t st) {
+                           int* status, const CUtensorMap& tm, cudaStream_t st,
+                           KernelTimer* timer) {
   const size_t sm = tc_smem_bytes<NP, TMA>();
   cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
   sketch_tc_kernel<NP, TMA><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(a, w, drain_blocks,
                                                                               status, tm);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (timer) e = timer->mark(st);
+  return e;
 }
 
 }  // namespace
 
 cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
-                             int drain_blocks, int* status, cudaStream_t st) {
+                             int drain_blocks, int* status, cudaStream_t st, KernelTimer* timer) {
   if (w.ncols <= 0) return cudaSuccess;
   if (w.ncols > kTcMaxTiles * TCOLS || a.l > LP) return cudaErrorInvalidValue;
   const int64_t nrb = (a.m + TR - 1) / TR;
@@ -743,11 +738,11 @@ cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, 
   const bool tma = make_tmap(a, w, &tm);
   cudaError_t e;
   if (npieces == 1)
-    e = tma ? launch_variant<1, true>(a, w, grid, drain_blocks, status, tm, st)
-            : launch_variant<1, false>(a, w, grid, drain_blocks, status, tm, st);
+    e = tma ? launch_variant<1, true>(a, w, grid, drain_blocks, status, tm, st, timer)
+            : launch_variant<1, false>(a, w, grid, drain_blocks, status, tm, st, timer);
   else
-    e = tma ? launch_variant<2, true>(a, w, grid, drain_blocks, status, tm, st)
-            : launch_variant<2, false>(a, w, grid, drain_blocks, status, tm, st);
+    e = tma ? launch_variant<2, true>(a, w, grid, drain_blocks, status, tm, st, timer)
+            : launch_variant<2, false>(a, w, grid, drain_blocks, status, tm, st, timer);
   if (e != cudaSuccess) return e;
   const int tot = a.l * w.ncols;
   wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(a.wpart, grid, a.l, w.ncols, nrb, a.W,

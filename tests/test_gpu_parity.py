@@ -332,3 +332,29 @@ def test_tensor_core_sketch_feeds(monkeypatch, tma):
     assert rel(Y2.cpu().double().numpy(), Yo) <= 1e-5
     assert np.array_equal(Ac2.cpu().numpy(), A.cpu().numpy()[rows])
     sk.close()
+
+
+# ------------------------------------------------------------ kernel timing
+
+def test_kernel_timing_counts_launches():
+    """id_timing_enable / id_timing_read: one event pair per launch of the
+    fused sketch kernel and of the error-pass kernel, reset on read."""
+    from paper_1905_13257_gb300 import IdError
+    grid, n = (16, 12, 16), 300
+    A = channel_field(grid, 3, n, seed=5, dtype=torch.float32, device=DEV)
+    sk = _sk(m=A.shape[0], n_max=n, k=8, l=30, seed=1, dtype=torch.float32, window_cols=n)
+    with pytest.raises(IdError) as e:
+        sk.read_timing("sketch")
+    assert e.value.status == 2
+    sk.timing(True)
+    stream(sk, A, [32] * 9 + [12])
+    sk.flush()
+    ms, cnt = sk.read_timing("sketch")
+    assert cnt == 1 and ms > 0.0          # 300 columns: one tensor-core window
+    assert sk.read_timing("sketch") == (0.0, 0)
+    J, P, kout = sk.factor()
+    sk.reconstruct_error(A, J[:kout], P[:kout])
+    ms, cnt = sk.read_timing("recon")
+    assert cnt == 1 and ms > 0.0
+    sk.timing(False)
+    sk.close()
