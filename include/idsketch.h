@@ -175,6 +175,45 @@ id_status id_reconstruct_error_noalloc(const void* d_A, int64_t lda, int64_t m, 
                                        int32_t k, double* rel_fro, double* rel_max,
                                        void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Single-pass ID (Algorithm 6, Sec. 2.6; eq. eqn:single_ID), column form:
+ *   A ~ M A_c(:, J_c) P_c,
+ * (J_c, P_c) from id_coarse_factor and M (m x m_c) the coarse-to-fine
+ * interpolation of Algorithm 6 step 4: trilinear on the mesh, 8 coarse points
+ * per fine point (a fine index on a coarse point takes it alone; between two
+ * coarse points the weight follows the physical distance; past the last
+ * coarse point a periodic direction wraps to point 0 at x_0 + period and a
+ * non-periodic one extrapolates linearly from its last two coarse points).
+ * The fine skeleton is never read from A: only A_c is kept.
+ * ------------------------------------------------------------------- */
+
+/* Mesh of the grid (host arrays, copied): x[nx], y[ny], z[nz] strictly
+ * increasing coordinates of the grid indices; period[d] > 0 makes direction d
+ * periodic with that length (x_0 + period > x_last), 0 leaves it open.
+ * Requires want_coarse.  Allocates the interpolation tables and an
+ * m_c x 64 skeleton buffer on the first call.  Errors: ID_ERR_STATE (no
+ * coarse grid), ID_ERR_INVALID_ARG (NULL, non-increasing or non-finite
+ * coordinates, bad period), ID_ERR_OOM. */
+id_status id_set_mesh(id_sketch* h, const double* x, const double* y, const double* z,
+                      const double period[3]);
+
+/* S = M A_c(:, J_c): the single-pass ID's fine skeleton (m x kc, data type,
+ * column-major, leading dimension m) written to the device buffer d_S.  J_c:
+ * kc column indices of the streamed snapshots (host or device), 1 <= kc <= 64.
+ * Synchronises the stream.  Errors: ID_ERR_STATE (no mesh, no coarse grid or
+ * no columns yet), ID_ERR_INVALID_ARG (NULL, kc out of range, J_c outside
+ * the streamed columns), ID_ERR_CUDA. */
+id_status id_single_pass_lift(id_sketch* h, const int32_t* Jc, int32_t kc, void* d_S);
+
+/* Errors of the single-pass ID A_hat = M A_c(:, J_c) P_c against A (device,
+ * m x n, column-major, lda >= m, data type), one read of A: rel_fro =
+ * ||A - A_hat||_F / ||A||_F and rel_max = max |A_ij - A_hat_ij| / |A_ij| over
+ * A_ij != 0 (the metrics of Sec. 3).  P_c: kc x n FP64 row-major (host or
+ * device).  Errors as id_single_pass_lift, plus ID_ERR_TIMEOUT. */
+id_status id_single_pass_error(id_sketch* h, const void* d_A, int64_t lda, int64_t n,
+                               const int32_t* Jc, const double* Pc, int32_t kc, double* rel_fro,
+                               double* rel_max);
+
 /* Borrow the device buffers of the sketch (valid until reset/destroy):
  *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])
  *   Y  m x l, dtype, column-major (entry (i, s) at Y[i + s*m]); NULL unless want_Y

@@ -11,6 +11,9 @@ Modules
   interp_decomp  sketches, column-pivoted Householder QR, interpolation
                  matrix, deterministic / randomized / sub-sampled ID, error
                  metrics and the Theorem 2.1 bound (Sec. 2.4-2.5)
+  single_pass    the single-pass ID of Algorithm 6 (Sec. 2.6): the
+                 coarse-to-fine interpolation operator M on the mesh, the
+                 interpolated skeleton, its error and the Theorem 2.2 bound
 
 Parity status of each function is pinned by ``tests/test_oracle_*.py``; none
 is unpinned.
@@ -21,6 +24,8 @@ from .interp_decomp import (sketch, householder, cpqr, back_substitute,
                             interpolation_matrix, column_id, deterministic_id,
                             randomized_id, coarse_rows, subsampled_id, recon_error,
                             spectral_norm, theorem21_rho, RANK_TOL_FACTOR)
+from .single_pass import (axis_weights, coarse_to_fine, single_pass_id, single_pass_error,
+                          theorem22_bound)
 
 __all__ = [
     "philox4x32_10", "twelve_bit_fields", "bf16_round_f64", "gaussian_table",
@@ -28,5 +33,6 @@ __all__ = [
     "sketch", "householder", "cpqr", "back_substitute", "interpolation_matrix",
     "column_id", "deterministic_id", "randomized_id", "coarse_rows",
     "subsampled_id", "recon_error", "spectral_norm", "theorem21_rho",
-    "RANK_TOL_FACTOR",
+    "RANK_TOL_FACTOR", "axis_weights", "coarse_to_fine", "single_pass_id",
+    "single_pass_error", "theorem22_bound",
 ]

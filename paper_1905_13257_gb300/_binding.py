@@ -66,6 +66,11 @@ SIGNATURES = {
                                 C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "id_sketch_destroy": (None, [C.c_void_p]),
+    "id_set_mesh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "id_single_pass_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "id_single_pass_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                       C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "id_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "id_timing_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),

@@ -144,6 +144,37 @@ class IdSketch:
                 "id_reconstruct_error")
         return fro.value, mx.value
 
+    def set_mesh(self, x, y, z, periods=(0.0, 0.0, 0.0)):
+        """Grid coordinates for the single-pass ID's interpolation (id_set_mesh)."""
+        import numpy as np
+        arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z)]
+        per = np.ascontiguousarray(periods, dtype=np.float64)
+        B.check(self.lib.id_set_mesh(self.h, *[C.c_void_p(a.ctypes.data) for a in arrs],
+                                     C.c_void_p(per.ctypes.data)), "id_set_mesh")
+
+    def single_pass_lift(self, Jc, k=None):
+        """S = M A_c(:, J_c) (m x k, device, column-major): the single-pass ID's
+        fine skeleton (id_single_pass_lift)."""
+        k = int(Jc.numel()) if k is None else int(k)
+        Jc = Jc.to(torch.int32).contiguous()
+        S = torch.empty((k, self.m), dtype=self.dtype, device=self.stream.device)
+        B.check(self.lib.id_single_pass_lift(self.h, C.c_void_p(Jc.data_ptr()), k,
+                                             C.c_void_p(S.data_ptr())), "id_single_pass_lift")
+        return S.T
+
+    def single_pass_error(self, A, Jc, Pc, k=None):
+        """(rel_fro, rel_max) of A_hat = M A_c(:, J_c) P_c (id_single_pass_error)."""
+        ld = _colmajor(A, self.m)
+        k = int(Jc.numel()) if k is None else int(k)
+        Jc = Jc.to(torch.int32).contiguous()
+        Pc = Pc.to(torch.float64).contiguous()
+        fro, mx = C.c_double(), C.c_double()
+        B.check(self.lib.id_single_pass_error(self.h, C.c_void_p(A.data_ptr()), ld, A.shape[1],
+                                              C.c_void_p(Jc.data_ptr()),
+                                              C.c_void_p(Pc.data_ptr()), k, C.byref(fro),
+                                              C.byref(mx)), "id_single_pass_error")
+        return fro.value, mx.value
+
     def sketches(self):
         """Zero-copy views (W (l, n) FP64, Y (m, l) or None, A_c (m_c, n) or None)."""
         w, y, ac = C.c_void_p(), C.c_void_p(), C.c_void_p()

@@ -7,8 +7,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "idsk_internal.h"
 
@@ -88,7 +90,8 @@ void free_all(id_sketch* h) {
   void* ptrs[] = {h->d_omega, h->d_W, h->d_Y, h->d_Ac, h->d_work, h->d_R, h->d_P, h->d_J,
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gvec, h->d_hvec, h->d_vh, h->d_vl,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
-                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart};
+                  h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart,
+                  h->d_axis, h->d_Sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -196,6 +199,43 @@ id_status launch_pending(id_sketch* h) {
 id_status copy_out(id_sketch* h, void* dst, const void* src, size_t bytes) {
   if (!dst || bytes == 0) return ID_OK;
   IDSK_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->st));
+  return ID_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------- single-pass ID
+namespace {
+
+idsk::InterpGeom interp_geom(const id_sketch* h) {
+  idsk::InterpGeom g;
+  g.ax = h->d_axis;
+  g.ay = h->d_axis + h->cg.nx;
+  g.az = h->d_axis + h->cg.nx + h->cg.ny;
+  g.Sc = h->d_Sc;
+  g.nx = h->cg.nx;
+  g.ny = h->cg.ny;
+  g.nz = h->cg.nz;
+  g.cx = h->cg.cx;
+  g.cy = h->cg.cy;
+  g.cz = h->cg.cz;
+  return g;
+}
+
+// Common checks of the single-pass calls; copies J_c (host or device) to the
+// device and compacts the coarse skeleton A_c(:, J_c) into d_Sc.
+id_status stage_coarse_skeleton(id_sketch* h, const int32_t* Jc, int32_t kc) {
+  if (!h->cfg.want_coarse || !h->mesh_set) return ID_ERR_STATE;
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  if (h->n_seen == 0) return ID_ERR_STATE;
+  int32_t jh[kRecKMax];
+  IDSK_CUDA(h, cudaMemcpyAsync(jh, Jc, sizeof(int32_t) * kc, cudaMemcpyDefault, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  for (int u = 0; u < kc; ++u)
+    if (jh[u] < 0 || jh[u] >= h->n_seen) return ID_ERR_INVALID_ARG;
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_Jin, jh, sizeof(int32_t) * kc, cudaMemcpyHostToDevice, h->st));
+  IDSK_CUDA(h, launch_skeleton_compact(h->d_Ac, h->mc, h->cfg.dtype, h->d_Jin, kc, h->d_Sc, h->st));
   return ID_OK;
 }
 
@@ -474,6 +514,94 @@ id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64
   IDSK_CUDA(h, launch_recon_error(d_A, lda, h->m, n, h->cfg.dtype, h->d_Jin, h->d_Pin, k,
                                   h->d_part, h->rec_blocks, h->d_out3, h->d_status, h->st,
                                   h->timer_recon));
+  double o[3];
+  int32_t dst = 0;
+  IDSK_CUDA(h, cudaMemcpyAsync(o, h->d_out3, sizeof(o), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(&dst, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (dst) {
+    h->poisoned = true;
+    return ID_ERR_TIMEOUT;
+  }
+  if (rel_fro) *rel_fro = o[1] > 0.0 ? sqrt(o[0] / o[1]) : 0.0;
+  if (rel_max) *rel_max = o[2];
+  return ID_OK;
+}
+
+id_status id_set_mesh(id_sketch* h, const double* x, const double* y, const double* z,
+                      const double period[3]) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!h->cfg.want_coarse) return ID_ERR_STATE;
+  if (!x || !y || !z || !period) return ID_ERR_INVALID_ARG;
+  const double* c[3] = {x, y, z};
+  const int n[3] = {h->cg.nx, h->cg.ny, h->cg.nz};
+  const int sd[3] = {h->cg.sx, h->cg.sy, h->cg.sz};
+  std::vector<idsk::AxisW> tab;
+  for (int d = 0; d < 3; ++d) {
+    if (!(period[d] >= 0.0) || !std::isfinite(period[d])) return ID_ERR_INVALID_ARG;
+    for (int i = 0; i < n[d]; ++i) {
+      if (!std::isfinite(c[d][i])) return ID_ERR_INVALID_ARG;
+      if (i > 0 && !(c[d][i] > c[d][i - 1])) return ID_ERR_INVALID_ARG;   // increasing
+    }
+    if (period[d] > 0.0 && !(c[d][0] + period[d] > c[d][n[d] - 1])) return ID_ERR_INVALID_ARG;
+    const size_t off = tab.size();
+    tab.resize(off + n[d]);
+    idsk::build_axis_weights(c[d], n[d], sd[d], period[d], tab.data() + off);
+  }
+  if (!h->d_axis) {
+    Allocator al;
+    al.get(&h->d_axis, tab.size());
+    al.get((char**)&h->d_Sc, (size_t)h->mc * idsk::kSkelLd * h->esz);
+    if (al.st != ID_OK) {
+      if (h->d_axis) cudaFree(h->d_axis);
+      if (h->d_Sc) cudaFree(h->d_Sc);
+      h->d_axis = nullptr;
+      h->d_Sc = nullptr;
+      return al.st;
+    }
+  }
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_axis, tab.data(), sizeof(idsk::AxisW) * tab.size(),
+                               cudaMemcpyHostToDevice, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  h->mesh_set = true;
+  return ID_OK;
+}
+
+id_status id_single_pass_lift(id_sketch* h, const int32_t* Jc, int32_t kc, void* d_S) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!Jc || !d_S || kc < 1 || kc > kRecKMax) return ID_ERR_INVALID_ARG;
+  id_status s = stage_coarse_skeleton(h, Jc, kc);
+  if (s != ID_OK) return s;
+  IDSK_CUDA(h, launch_single_pass_lift(interp_geom(h), h->m, h->cfg.dtype, kc, d_S, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  return ID_OK;
+}
+
+id_status id_single_pass_error(id_sketch* h, const void* d_A, int64_t lda, int64_t n,
+                               const int32_t* Jc, const double* Pc, int32_t kc, double* rel_fro,
+                               double* rel_max) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!d_A || !Jc || !Pc || lda < h->m || n < 1 || kc < 1 || kc > kRecKMax)
+    return ID_ERR_INVALID_ARG;
+  id_status s = stage_coarse_skeleton(h, Jc, kc);
+  if (s != ID_OK) return s;
+  if ((int64_t)kc * n > h->pin_cap) {
+    if (h->d_Pin) cudaFree(h->d_Pin);
+    h->d_Pin = nullptr;
+    h->pin_cap = 0;
+    Allocator al;
+    al.get(&h->d_Pin, (size_t)kc * n);
+    if (al.st != ID_OK) return al.st;
+    h->pin_cap = (int64_t)kc * n;
+  }
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_Pin, Pc, sizeof(double) * kc * n, cudaMemcpyDefault, h->st));
+  const idsk::InterpGeom g = interp_geom(h);
+  IDSK_CUDA(h, launch_recon_error(d_A, lda, h->m, n, h->cfg.dtype, h->d_Jin, h->d_Pin, kc,
+                                  h->d_part, h->rec_blocks, h->d_out3, h->d_status, h->st,
+                                  nullptr, &g));
   double o[3];
   int32_t dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(o, h->d_out3, sizeof(o), cudaMemcpyDeviceToHost, h->st));

@@ -108,6 +108,58 @@ struct SketchArgs {
   double* wpart;        // tensor-core kernel: per-CTA FP64 W^T slabs [nsm][64][512]
 };
 
+// ------------------------------------------------ single-pass ID (Alg. 6)
+// Coarse-to-fine interpolation of one direction at fine index i: the value is
+// (1 - w) f[lo] + w f[hi] with lo, hi coarse indices (a fine index on a coarse
+// point has lo = hi, w = 0; a periodic direction wraps past its last coarse
+// point; a non-periodic one extrapolates from its last two coarse points).
+struct AxisW {
+  int32_t lo, hi;
+  double w;
+};
+
+// Trilinear interpolation of the coarse skeleton Sc = A_c(:, J_c) (m_c rows of
+// kSkelLd entries, row-major, data type) to fine row r.
+constexpr int kSkelLd = 64;
+struct InterpGeom {
+  const AxisW* ax = nullptr;   // nx entries
+  const AxisW* ay = nullptr;   // ny entries
+  const AxisW* az = nullptr;   // nz entries
+  const void* Sc = nullptr;    // null: no interpolation (gather A(:, J) instead)
+  int32_t nx = 0, ny = 0, nz = 0, cx = 0, cy = 0, cz = 0;
+};
+
+// The 8 corners of fine row r = ((c ny + j) nz + kz) nx + i: coarse rows
+// ((c cy + jy) cz + kc) cx + ic and their trilinear weights, formed in the
+// arithmetic of W (the data type of the interpolation).
+template <typename W>
+__host__ __device__ inline void interp_corners(int64_t r, const InterpGeom& g, int64_t (&idx)[8],
+                                               W (&w)[8]) {
+  const int64_t i = r % g.nx;
+  int64_t rest = r / g.nx;
+  const int64_t kz = rest % g.nz;
+  rest /= g.nz;
+  const int64_t j = rest % g.ny;
+  const int64_t c = rest / g.ny;
+  const AxisW X = g.ax[i], Y = g.ay[j], Z = g.az[kz];
+  int q = 0;
+  for (int b = 0; b < 2; ++b) {
+    const int64_t iy = b ? Y.hi : Y.lo;
+    const W fy = b ? (W)Y.w : (W)1 - (W)Y.w;
+    for (int d = 0; d < 2; ++d) {
+      const int64_t iz = d ? Z.hi : Z.lo;
+      const W fz = d ? (W)Z.w : (W)1 - (W)Z.w;
+      for (int a = 0; a < 2; ++a) {
+        const int64_t ix = a ? X.hi : X.lo;
+        const W fx = a ? (W)X.w : (W)1 - (W)X.w;
+        idx[q] = ((c * g.cy + iy) * g.cz + iz) * g.cx + ix;
+        w[q] = fx * fy * fz;
+        ++q;
+      }
+    }
+  }
+}
+
 // CUDA events recorded around the main kernel of a launcher, on the launching
 // stream (optional measurement; the launchers take a null pointer when off).
 struct KernelTimer {
@@ -213,6 +265,11 @@ struct id_sketch {
   // kernel
   idsk::KernelTimer* timer_sketch = nullptr;
   idsk::KernelTimer* timer_recon = nullptr;
+  // id_set_mesh: per-direction interpolation tables and the compact coarse
+  // skeleton of the single-pass ID
+  idsk::AxisW* d_axis = nullptr;   // nx + ny + nz entries
+  void* d_Sc = nullptr;            // m_c x kSkelLd, dtype
+  bool mesh_set = false;
 };
 
 // ------------------------------------------------------------- launchers
@@ -233,11 +290,17 @@ cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
                                double* out3, int* status, cudaStream_t st,
-                               KernelTimer* timer = nullptr);
+                               KernelTimer* timer = nullptr, const InterpGeom* interp = nullptr);
 int recon_tc_grid(int64_t m, int64_t n, int nsm);
 cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
                             const double* P, int k, double* part, int grid, int* status,
-                            cudaStream_t st, KernelTimer* timer = nullptr);
+                            cudaStream_t st, KernelTimer* timer = nullptr,
+                            const InterpGeom* interp = nullptr);
+void build_axis_weights(const double* x, int n, int stride, double period, AxisW* out);
+cudaError_t launch_skeleton_compact(const void* Ac, int64_t mc, int dtype, const int* Jc, int k,
+                                    void* Sc, cudaStream_t st);
+cudaError_t launch_single_pass_lift(const InterpGeom& g, int64_t m, int dtype, int k, void* S,
+                                    cudaStream_t st);
 void gaussian_table_host(float* vals, uint16_t* bits);
 void count_launches(int64_t n);
 }  // namespace idsk

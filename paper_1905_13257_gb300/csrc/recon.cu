@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(NT) recon_kernel(const T* __restrict__ A, int6
                                                    int64_t m, int64_t n,
                                                    const int* __restrict__ J,
                                                    const double* __restrict__ P, int k,
-                                                   double* __restrict__ part) {
+                                                   double* __restrict__ part, InterpGeom geo) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* sk = reinterpret_cast<T*>(smem);   // k x TM   : A(R, J)
   T* as = sk + kRecKMax * TM;           // TC x (TM+1)
@@ -54,9 +54,25 @@ __global__ void __launch_bounds__(NT) recon_kernel(const T* __restrict__ A, int6
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * TM;
     __syncthreads();
-    for (int e = t; e < k * TM; e += NT) {
-      const int u = e / TM, r = e % TM;
-      sk[e] = (r0 + r < m) ? A[(r0 + r) + (int64_t)Js[u] * lda] : T(0);
+    if (geo.Sc == nullptr) {
+      for (int e = t; e < k * TM; e += NT) {
+        const int u = e / TM, r = e % TM;
+        sk[e] = (r0 + r < m) ? A[(r0 + r) + (int64_t)Js[u] * lda] : T(0);
+      }
+    } else {   // single-pass ID: skeleton rows interpolated from the coarse ones
+      const int r = t % TM;
+      int64_t idx[8];
+      T w[8];
+      if (r0 + r < m) interp_corners<T>(r0 + r, geo, idx, w);
+      const T* sc = reinterpret_cast<const T*>(geo.Sc);
+      for (int u = t / TM; u < k; u += NT / TM) {
+        T acc = T(0);
+        if (r0 + r < m) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc += w[q] * sc[idx[q] * kSkelLd + u];
+        }
+        sk[u * TM + r] = acc;
+      }
     }
     for (int64_t cc = 0; cc < n; cc += TC) {
       __syncthreads();
@@ -149,7 +165,9 @@ size_t recon_smem(void) {
 
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
-                               double* out3, int* status, cudaStream_t st, KernelTimer* timer) {
+                               double* out3, int* status, cudaStream_t st, KernelTimer* timer,
+                               const InterpGeom* interp) {
+  const InterpGeom geo = interp ? *interp : InterpGeom{};
   cudaError_t e;
   if (dtype == ID_F32 && m >= 128) {
     // FP32 data: tensor-core pass (products split into bf16 pieces)
@@ -160,7 +178,7 @@ cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n,
     const int grid = std::min(recon_tc_grid(m, n, nsm), nblk);
     if (grid * 1 < (int)((n + 255) / 256)) return cudaErrorInvalidValue;
     e = launch_recon_tc(reinterpret_cast<const float*>(A), lda, m, n, J, P, k, part, grid,
-                        status, st, timer);
+                        status, st, timer, interp);
     if (e != cudaSuccess) return e;
     recon_finalize_kernel<<<1, 32, 0, st>>>(part, grid, out3);
     count_launches(1);
@@ -175,14 +193,14 @@ cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n,
                              (int)sm);
     if (e != cudaSuccess) return e;
     recon_kernel<double><<<grid, NT, sm, st>>>(reinterpret_cast<const double*>(A), lda, m, n, J,
-                                               P, k, part);
+                                               P, k, part, geo);
   } else {
     const size_t sm = recon_smem<float>();
     e = cudaFuncSetAttribute(recon_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm);
     if (e != cudaSuccess) return e;
     recon_kernel<float><<<grid, NT, sm, st>>>(reinterpret_cast<const float*>(A), lda, m, n, J, P,
-                                              k, part);
+                                              k, part, geo);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

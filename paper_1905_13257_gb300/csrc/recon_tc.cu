@@ -104,7 +104,7 @@ __device__ __forceinline__ void split3(double x, uint16_t& p0, uint16_t& p1, uin
 __global__ void __launch_bounds__(NTHREADS, 1)
     recon_tc_kernel(const float* __restrict__ A, int64_t lda, int64_t m, int n,
                     const int* __restrict__ J, const double* __restrict__ P, int k,
-                    double* __restrict__ part, int* __restrict__ status) {
+                    double* __restrict__ part, int* __restrict__ status, InterpGeom geo) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t s_p = base;                       // P pieces: 3 x 32 KB
@@ -253,8 +253,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t r = (rb_begin + i) * TR + rl;
       const bool rok = r < m;
       float x[KP];
+      if (geo.Sc == nullptr) {
 #pragma unroll
-      for (int t = 0; t < KP; ++t) x[t] = (t < k && rok) ? A[r + (int64_t)Js[t] * lda] : 0.f;
+        for (int t = 0; t < KP; ++t) x[t] = (t < k && rok) ? A[r + (int64_t)Js[t] * lda] : 0.f;
+      } else {   // single-pass ID: the skeleton row interpolated from the coarse one
+#pragma unroll
+        for (int t = 0; t < KP; ++t) x[t] = 0.f;
+        if (rok) {
+          int64_t idx[8];
+          float w[8];
+          interp_corners<float>(r, geo, idx, w);
+          const float4* sc = reinterpret_cast<const float4*>(geo.Sc);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4* row = sc + idx[q] * (kSkelLd / 4);
+#pragma unroll
+            for (int t4 = 0; t4 < KP / 4; ++t4) {
+              if (4 * t4 < k) {
+                const float4 v = row[t4];
+                x[4 * t4] = fmaf(w[q], v.x, x[4 * t4]);
+                x[4 * t4 + 1] = fmaf(w[q], v.y, x[4 * t4 + 1]);
+                x[4 * t4 + 2] = fmaf(w[q], v.z, x[4 * t4 + 2]);
+                x[4 * t4 + 3] = fmaf(w[q], v.w, x[4 * t4 + 3]);
+              }
+            }
+          }
+        }
+      }
       if (i >= 2 && !mbar_wait(bar(B_SE0 + b), ((i >> 1) - 1) & 1, abort_flag, 64)) break;
       uint8_t* sbp = sm_gen + (size_t)b * 3u * S_PIECE;
 #pragma unroll
@@ -342,13 +367,14 @@ int recon_tc_grid(int64_t m, int64_t n, int nsm) {
 
 cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
                             const double* P, int k, double* part, int grid, int* status,
-                            cudaStream_t st, KernelTimer* timer) {
+                            cudaStream_t st, KernelTimer* timer, const InterpGeom* interp) {
   const size_t sm = 1024 + 3u * P_PIECE + 6u * S_PIECE + NBAR * 8 + 16;
   cudaError_t e = cudaFuncSetAttribute(recon_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
-  recon_tc_kernel<<<grid, NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status);
+  const InterpGeom geo = interp ? *interp : InterpGeom{};
+  recon_tc_kernel<<<grid, NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status, geo);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (timer) e = timer->mark(st);

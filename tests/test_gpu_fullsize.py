@@ -7,8 +7,9 @@
   (18.9 GB), chunks of 32 aggregated into one window, l = 60, k = 50, coarse
   4x: sampled columns of W and rows of Y against the oracle's one-by-one
   products, the exact coarse gather, the pivoted QRs against the oracle on
-  the same (validated) inputs, and the reconstruction error against the
-  oracle's exact sum taken over row chunks.
+  the same (validated) inputs, and the reconstruction errors of the
+  sub-sampled and the single-pass ID against the oracle's exact sums taken
+  over row chunks.
 """
 import numpy as np
 import pytest
@@ -78,7 +79,7 @@ def streamed_case():
     Jc, Pc, kc = sk.coarse_factor()
     fro, mx = sk.reconstruct_error(A, J[:kout], P[:kout])
     W, Y, Ac = sk.sketches()
-    out = dict(A=A, grid=grid, nc=nc, n=n, k=k, l=l, seed=seed, m=m, J=J.cpu().numpy(),
+    out = dict(sk=sk, A=A, grid=grid, nc=nc, n=n, k=k, l=l, seed=seed, m=m, J=J.cpu().numpy(),
                P=P.cpu().numpy(), kout=kout, Jc=Jc.cpu().numpy(), Pc=Pc.cpu().numpy(), kc=kc,
                fro=fro, mx=mx, W=W.cpu().numpy().copy(), Y=Y, Ac=Ac.cpu().numpy().copy())
     yield out
@@ -144,3 +145,37 @@ def test_streamed_reconstruction_error_exact_sum(streamed_case):
     fo = np.sqrt(ss_res / ss_a)
     assert abs(c["fro"] - fo) <= 1e-4 * fo + 2e-6
     assert abs(c["mx"] - rmax) <= 1e-3 * rmax
+
+
+def test_streamed_single_pass_id(streamed_case):
+    """Algorithm 6 at full size: the lifted skeleton M A_c(:, J_c) and the
+    single-pass error against the oracle's operator M (all 4.7M rows)."""
+    import oracle.single_pass as osp
+    from synthetic.channel import LX, LZ, wall_normal_points
+    c = streamed_case
+    sk, A, grid, kc = c["sk"], c["A"], c["grid"], c["kc"]
+    nx, ny, nz = grid
+    coords = (np.arange(nx) * (LX / nx), wall_normal_points(ny), np.arange(nz) * (LZ / nz))
+    per = (LX, 0.0, LZ)
+    sk.set_mesh(*coords, per)
+    Jc = torch.as_tensor(c["Jc"][:kc])
+    Pc = torch.as_tensor(c["Pc"][:kc])
+    S = sk.single_pass_lift(Jc, kc).cpu().double().numpy()
+    fro, mx = sk.single_pass_error(A, Jc, Pc)
+    M = osp.coarse_to_fine(grid, c["nc"], (4, 4, 4), coords, per)
+    So = M @ c["Ac"].astype(np.float64)[:, c["Jc"][:kc]]
+    assert rel(S, So) <= 1e-6
+    ss_res = ss_a = 0.0
+    rmax = 0.0
+    Pn = c["Pc"][:kc]
+    for r0 in range(0, c["m"], 262_144):
+        blk = A[r0:r0 + 262_144].cpu().double().numpy()
+        R = blk - So[r0:r0 + 262_144] @ Pn
+        ss_res += float(np.sum(R * R))
+        ss_a += float(np.sum(blk * blk))
+        nzm = blk != 0
+        if np.any(nzm):
+            rmax = max(rmax, float(np.max(np.abs(R[nzm]) / np.abs(blk[nzm]))))
+    fo = np.sqrt(ss_res / ss_a)
+    assert abs(fro - fo) <= 1e-4 * fo + 2e-6
+    assert abs(mx - rmax) <= 1e-3 * rmax
