@@ -25,11 +25,12 @@
 // the next pivot.  Every sum runs in a fixed order (CTA-ordered partials), so
 // results do not depend on scheduling.
 //
-// Precision: FP64 throughout, except the product A_c^T u.  For FP32 data it
-// runs on the FP32 units as exact FP32 products of A_c with u split into an
-// FP32 pair, summed as FP32 pairs (about 48 significant bits): FP64
-// arithmetic on this GPU is too slow for a pass over A_c at memory speed,
-// while the FP32 units are not.
+// Precision: the O(m_c n) product A_c^T u and the O(m_c s) work of each
+// step (u, V_s^T u, ||u||^2, the reflectors V themselves) run on the FP32
+// units in FP32-pair arithmetic (value = hi + lo, exact products by FMA,
+// TwoSum accumulation: about 48 significant bits); the Householder scalars,
+// F, R and the norms are FP64.  FP64 arithmetic on this GPU (1.25 TFLOP/s)
+// is too slow for these passes at memory speed, its FP32 units are not.
 #include <float.h>
 #include <stdlib.h>
 
@@ -202,6 +203,26 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
   lo += err + bl;
 }
 
+// FP32-pair numbers (value h + l, |l| <= ulp(h) / 2 after normalisation):
+// about 48 significant bits on the FP32 units.
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double df_val(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_norm(float h, float l) {   // |h| >= |l|
+  const float s = h + l;
+  return make_float2(s, l - (s - h));
+}
+// a * b: exact product of the high parts (FMA), cross terms in FP32
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return df_norm(p, e);
+}
+
 // True in every thread of the one CTA that finished last (release/acquire
 // through a device-scope counter, which that CTA resets for the next launch).
 __device__ bool last_cta(unsigned* counter) {
@@ -228,81 +249,125 @@ __device__ bool last_cta(unsigned* counter) {
 template <typename T>
 __global__ void __launch_bounds__(ST_THREADS) step_kernel(
     const T* __restrict__ Ac, int64_t mc, int n, int s, int64_t rpc,
-    double* __restrict__ V, const double* __restrict__ F, int64_t ldf,
+    float2* __restrict__ V, const double* __restrict__ F, int64_t ldf,
     float* __restrict__ uh, float* __restrict__ ul, double* __restrict__ hpart,
     double* __restrict__ hvec, double* __restrict__ Rc, double* __restrict__ cscal,
     int* __restrict__ cint) {
-  __shared__ double fp[kLMax];
-  __shared__ double ud[ST_THREADS];
-  __shared__ double sh[33];
+  __shared__ float2 fp[kLMax];
+  __shared__ float2 ud[ST_THREADS];
   if (cint[CI_STOP]) return;
   const int p = cint[CI_P];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (blockIdx.x == 0 && tid == 0) cint[CI_PICKED] = 0;   // read by this step's recompute
-  for (int t = tid; t < s; t += ST_THREADS) fp[t] = F[(int64_t)t * ldf + p];
+  for (int t = tid; t < s; t += ST_THREADS) fp[t] = df_of(F[(int64_t)t * ldf + p]);
   const double psig = s > 0 ? cscal[CS_SIGMA] : 0.0;
-  const double prcp = (s > 0 && psig != 0.0) ? 1.0 / cscal[CS_DEN] : 0.0;   // v = u / den
+  const float2 prcp = df_of((s > 0 && psig != 0.0) ? 1.0 / cscal[CS_DEN] : 0.0);   // v = u / den
   __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int64_t r1 = (mc < r0 + rpc) ? mc : r0 + rpc;
-  double sig = 0.0;
-  double hacc[kLMax / 8];
+  float2 sig = make_float2(0.f, 0.f);
+  float2 hacc[kLMax / 8];
 #pragma unroll
-  for (int q = 0; q < kLMax / 8; ++q) hacc[q] = 0.0;
+  for (int q = 0; q < kLMax / 8; ++q) hacc[q] = make_float2(0.f, 0.f);
   for (int64_t c0 = r0; c0 < r1; c0 += ST_THREADS) {
     const int nrow = (int)((r1 - c0) < ST_THREADS ? (r1 - c0) : ST_THREADS);
     const int64_t i = c0 + tid;
-    double uu = 0.0;
+    float2 uu = make_float2(0.f, 0.f);
     if (tid < nrow) {
       if (s > 0) {   // v_{s-1}: zero above row s-1, one at it, u / den below
-        double* vp = V + (int64_t)(s - 1) * mc + i;
+        float2* vp = V + (int64_t)(s - 1) * mc + i;
         if (i == s - 1)
-          *vp = 1.0;
+          *vp = make_float2(1.f, 0.f);
         else if (i > s - 1)
-          *vp *= prcp;
+          *vp = df_mul(*vp, prcp);
       }
-      double u = 0.0;
+      float2 u = make_float2(0.f, 0.f);
       if (i >= s) {
-        u = (double)Ac[i + (int64_t)p * mc];
-        for (int t = 0; t < s; ++t) u -= V[(int64_t)t * mc + i] * fp[t];
+        u = df_of((double)Ac[i + (int64_t)p * mc]);
+        for (int t0 = 0; t0 < s; t0 += 8) {   // 8 loads of V in flight, then the sums
+          float2 vv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            vv[q] = t0 + q < s ? V[(int64_t)(t0 + q) * mc + i] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (t0 + q < s) {
+              const float2 pr = df_mul(vv[q], fp[t0 + q]);
+              df_add(u.x, u.y, -pr.x, -pr.y);
+            }
+          }
+        }
+        u = df_norm(u.x, u.y);
       }
       V[(int64_t)s * mc + i] = u;
-      uu = i > s ? u : 0.0;
-      const float hi = (float)uu;
-      uh[i] = hi;
-      ul[i] = (float)(uu - (double)hi);
+      if (i > s) uu = u;
+      uh[i] = uu.x;
+      ul[i] = uu.y;
     }
     ud[tid] = uu;
-    sig += uu * uu;
+    const float2 u2 = df_mul(uu, uu);
+    df_add(sig.x, sig.y, u2.x, u2.y);
     __syncthreads();
     // V_s^T u: warp w takes t = w + 8q, each lane keeps partials over its rows
 #pragma unroll
     for (int q = 0; q < kLMax / 8; ++q) {
       const int t = warp + 8 * q;
       if (t < s) {
-        const double* vc = V + (int64_t)t * mc + c0;
-        for (int k = lane; k < nrow; k += 32) hacc[q] += vc[k] * ud[k];
+        const float2* vc = V + (int64_t)t * mc + c0;
+        for (int k0 = 0; k0 < nrow; k0 += 128) {   // 4 rows per lane in flight
+          float2 vv[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = k0 + 32 * e + lane;
+            vv[e] = k < nrow ? vc[k] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = k0 + 32 * e + lane;
+            if (k < nrow) {
+              const float2 pr = df_mul(vv[e], ud[k]);
+              df_add(hacc[q].x, hacc[q].y, pr.x, pr.y);
+            }
+          }
+        }
       }
     }
     __syncthreads();
   }
+  // warp sums of the pair partials (fixed shuffle tree)
 #pragma unroll
-  for (int q = 0; q < kLMax / 8; ++q)
-    if (warp + 8 * q < s) hacc[q] = warp_sum(hacc[q]);
-  sig = block_sum(sig, sh);
-  // partials stored as FP32 pairs (split here, in every CTA, so that the
-  // last CTA sums them on the FP32 units)
+  for (int q = 0; q < kLMax / 8; ++q) {
+    if (warp + 8 * q < s) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hacc[q].x, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, hacc[q].y, o);
+        df_add(hacc[q].x, hacc[q].y, oh, ol);
+      }
+      hacc[q] = df_norm(hacc[q].x, hacc[q].y);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sig.x, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, sig.y, o);
+    df_add(sig.x, sig.y, oh, ol);
+  }
+  __shared__ float2 sig_w[ST_THREADS / 32];
+  if (lane == 0) sig_w[warp] = sig;
+  __syncthreads();
+  // partials stored as FP32 pairs, summed by the last CTA on the FP32 units
   float2* hp = reinterpret_cast<float2*>(hpart) + (int64_t)blockIdx.x * HP;
-  auto split = [](double x) {
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
-  };
   if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < kLMax / 8; ++q)
-      if (warp + 8 * q < s) hp[warp + 8 * q] = split(hacc[q]);
+      if (warp + 8 * q < s) hp[warp + 8 * q] = hacc[q];
   }
-  if (tid == 0) hp[kLMax] = split(sig);
+  if (tid == 0) {
+    float2 a = sig_w[0];
+    for (int w = 1; w < ST_THREADS / 32; ++w) df_add(a.x, a.y, sig_w[w].x, sig_w[w].y);
+    hp[kLMax] = df_norm(a.x, a.y);
+  }
   if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_STEP))) return;
 
   // ---- last CTA: Householder scalars and h = V_s^T v_s.  Warp w sums the
@@ -342,7 +407,7 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
   }
   __syncthreads();
   const double sigma = hs[kLMax];
-  const double alpha = V[(int64_t)s * mc + s];
+  const double alpha = df_val(V[(int64_t)s * mc + s]);
   double beta = alpha, tau = 0.0, den = 0.0;
   if (sigma != 0.0) {
     const double nrm = sqrt(alpha * alpha + sigma);
@@ -352,7 +417,7 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
   }
   const double rden = sigma != 0.0 ? 1.0 / den : 0.0;
   for (int t = tid; t < s; t += ST_THREADS) {
-    const double vst = V[(int64_t)t * mc + s];   // v_t[s]
+    const double vst = df_val(V[(int64_t)t * mc + s]);   // v_t[s]
     hvec[t] = vst + hs[t] * rden;
   }
   if (tid == 0) {
@@ -375,7 +440,7 @@ constexpr int GV_THREADS = 256;
 template <typename T>
 __global__ void __launch_bounds__(GV_THREADS) gemv_kernel(
     const T* __restrict__ Ac, int64_t mc, int n, int s, int64_t chunk, int vec,
-    const float* __restrict__ uh, const float* __restrict__ ul, const double* __restrict__ V,
+    const float* __restrict__ uh, const float* __restrict__ ul,
     double* __restrict__ gpart, const int* __restrict__ cint) {
   __shared__ double sh[GCOLS][GV_THREADS / 32];
   if (cint[CI_STOP]) return;
@@ -442,11 +507,10 @@ __global__ void __launch_bounds__(GV_THREADS) gemv_kernel(
 #pragma unroll
     for (int q = 0; q < GCOLS; ++q) r[q] = (double)hi[q] + (double)lo[q];
   } else {
-    const double* u = V + (int64_t)s * mc;   // zero at and above row s is masked below
 #pragma unroll
     for (int q = 0; q < GCOLS; ++q) r[q] = 0.0;
     for (int64_t i = i0 + tid; i < i1; i += GV_THREADS) {
-      const double b = i > s ? u[i] : 0.0;
+      const double b = (double)uh[i] + (double)ul[i];   // zero at and above row s
 #pragma unroll
       for (int q = 0; q < GCOLS; ++q) r[q] = fma((double)cols[q][i], b, r[q]);
     }
@@ -655,7 +719,7 @@ __global__ void norms_from_parts_kernel(const double* __restrict__ part, int64_t
 constexpr int FIN_COLS = 32;
 template <typename T>
 __global__ void __launch_bounds__(256) finalize_kernel(
-    const T* __restrict__ Ac, int64_t mc, int n, int s, int G, const double* __restrict__ V,
+    const T* __restrict__ Ac, int64_t mc, int n, int s, int G, const float2* __restrict__ V,
     double* __restrict__ F, int64_t ldf, const double* __restrict__ gpart,
     const double* __restrict__ hvec, int* __restrict__ colpos, double* __restrict__ Rc,
     double* __restrict__ nu2, const double* __restrict__ nu20, int* __restrict__ rlist,
@@ -687,18 +751,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(
   }
   for (int t = tid; t < s; t += 256) {
     h[t] = hvec[t];
-    vrow[t] = V[(int64_t)t * mc + s];
+    vrow[t] = df_val(V[(int64_t)t * mc + s]);
   }
   __syncthreads();
   // F(j, 0:s) h and V(s, 0:s) F(j, 0:s)^T: warp w takes t = w, w + 8, ...
   {
     double fh = 0.0, rr = 0.0;
-    if (j < n)
-      for (int t = warp; t < s; t += 8) {
-        const double f = F[(int64_t)t * ldf + j];
-        fh += f * h[t];
-        rr += vrow[t] * f;
+    if (j < n) {
+      double fv[kLMax / 8];   // all loads of the thread in flight
+#pragma unroll
+      for (int q = 0; q < kLMax / 8; ++q) {
+        const int t = warp + 8 * q;
+        fv[q] = t < s ? F[(int64_t)t * ldf + j] : 0.0;
       }
+#pragma unroll
+      for (int q = 0; q < kLMax / 8; ++q) {
+        const int t = warp + 8 * q;
+        if (t < s) {
+          fh += fv[q] * h[t];
+          rr += vrow[t] * fv[q];
+        }
+      }
+    }
     pfh[warp][lane] = fh;
     prr[warp][lane] = rr;
   }
@@ -742,7 +816,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(
 // CTA then picks the pivot of step s + 1.
 template <typename T>
 __global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int n, int s, int kmax,
-                                 const double* __restrict__ V, const double* __restrict__ F,
+                                 const float2* __restrict__ V, const double* __restrict__ F,
                                  int64_t ldf, const int* __restrict__ rlist,
                                  double* __restrict__ nu2, double* __restrict__ nu20,
                                  int* __restrict__ colpos, int* __restrict__ Jc,
@@ -762,8 +836,8 @@ __global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int n, in
     double ss = 0.0;
     for (int64_t i = s + 1 + threadIdx.x; i < mc; i += blockDim.x) {
       double a = (double)Ac[i + (int64_t)j * mc];
-      for (int t = 0; t < s; ++t) a -= V[(int64_t)t * mc + i] * fj[t];
-      const double vs = V[(int64_t)s * mc + i] * rden;
+      for (int t = 0; t < s; ++t) a -= df_val(V[(int64_t)t * mc + i]) * fj[t];
+      const double vs = df_val(V[(int64_t)s * mc + i]) * rden;
       a -= vs * fj[s];
       ss += a * a;
     }
@@ -823,6 +897,7 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   const int vec = (sizeof(T) == 4 && (mc & 3) == 0) ? 1 : 0;
   const int ngroups = (n + GCOLS - 1) / GCOLS;
   const int fin_blocks = (n + FIN_COLS - 1) / FIN_COLS;
+  float2* V2 = reinterpret_cast<float2*>(h->d_V);   // reflectors as FP32 pairs
 
   // FP32 data with m_c a multiple of 4 streams A_c through bulk copies
   const bool streamed = vec && getenv("IDSKETCH_COARSE_STREAM") == nullptr;
@@ -847,7 +922,7 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < kmax; ++s) {
-    step_kernel<T><<<G, ST_THREADS, 0, st>>>(Ac, mc, n, s, rpc, h->d_V, h->d_F, ldf, h->d_vh,
+    step_kernel<T><<<G, ST_THREADS, 0, st>>>(Ac, mc, n, s, rpc, V2, h->d_F, ldf, h->d_vh,
                                              h->d_vl, h->d_upart, h->d_hvec, h->d_Rc,
                                              h->d_cscal, h->d_cint);
     if (streamed)
@@ -856,12 +931,12 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
           h->d_status, h->d_cint);
     else
       gemv_kernel<T><<<ngroups * RS, GV_THREADS, 0, st>>>(Ac, mc, n, s, chunk, vec, h->d_vh,
-                                                          h->d_vl, h->d_V, h->d_gvec, h->d_cint);
+                                                          h->d_vl, h->d_gvec, h->d_cint);
     finalize_kernel<T><<<fin_blocks, 256, 0, st>>>(
-        Ac, mc, n, s, streamed ? -SG : RS, h->d_V, h->d_F, ldf, h->d_gvec, h->d_hvec,
+        Ac, mc, n, s, streamed ? -SG : RS, V2, h->d_F, ldf, h->d_gvec, h->d_hvec,
         h->d_colposc, h->d_Rc, h->d_nu2, h->d_nu20, h->d_rlist, kmax, h->d_Jc, h->d_cscal,
         h->d_cint);
-    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, n, s, kmax, h->d_V, h->d_F, ldf, h->d_rlist,
+    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, n, s, kmax, V2, h->d_F, ldf, h->d_rlist,
                                             h->d_nu2, h->d_nu20, h->d_colposc, h->d_Jc,
                                             h->d_cscal, h->d_cint);
     count_launches(4);

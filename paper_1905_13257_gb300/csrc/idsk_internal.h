@@ -237,7 +237,7 @@ struct id_sketch {
   int* d_colpos = nullptr;    // n_max
   int* d_kout = nullptr;      // 1
   // coarse workspace (allocated on first id_coarse_factor)
-  double* d_V = nullptr;      // mc x k
+  double* d_V = nullptr;      // mc x k: reflectors as FP32 pairs (8 bytes each)
   double* d_F = nullptr;      // n_max x k
   double* d_nu2 = nullptr;    // n_max
   double* d_nu20 = nullptr;   // n_max
