@@ -1,6 +1,7 @@
 // Internal declarations of the idsketch library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -297,6 +298,11 @@ cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, c
                             cudaStream_t st, KernelTimer* timer = nullptr,
                             const InterpGeom* interp = nullptr);
 void build_axis_weights(const double* x, int n, int stride, double period, AxisW* out);
+// Tensor map of an FP32 column-major matrix (rows contiguous, leading
+// dimension ld), boxes of box_rows x box_cols, zero fill outside; false when
+// it cannot be built (alignment, no driver entry point).
+bool make_tmap_f32_2d(const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                      int box_cols, CUtensorMap* tm);
 cudaError_t launch_skeleton_compact(const void* Ac, int64_t mc, int dtype, const int* Jc, int k,
                                     void* Sc, cudaStream_t st);
 cudaError_t launch_single_pass_lift(const InterpGeom& g, int64_t m, int dtype, int k, void* S,

@@ -22,10 +22,17 @@
 //   warps 8-11  gather A(R, J): one row per thread, all k loads of the row
 //               issued at once, split, store the pieces (double-buffered)
 //   warp 12     TMEM allocation and the single-thread tcgen05.mma issue
-// 13 warps keep at most 4 warps per SM sub-partition (128 registers each).
+//   warp 13     (TMA form) streams A(R, C) in boxes of 128 rows x 32 columns
+//               through a 4-stage shared-memory ring for the epilogue
+// At most 4 warps per SM sub-partition (128 registers each).  The TMA form
+// (A 16-byte aligned, lda a multiple of 4) keeps 64 KB of A in flight per SM
+// and single-buffers the skeleton pieces to make room; the other form loads
+// A in the epilogue warps directly.
 // Waits are bounded as in the sketch kernel; on timeout the status word is
 // set and the host reports ID_ERR_TIMEOUT.
 #include <cuda_bf16.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -44,11 +51,16 @@ constexpr int NEPI = 8;
 constexpr int NGAT = 4;
 constexpr int MMA_WARP = NEPI + NGAT;    // 12
 constexpr int NTHREADS = (NEPI + NGAT + 1) * 32;
+constexpr int PROD_WARP = MMA_WARP + 1;  // TMA producer (TMA form only)
+constexpr int NTHREADS_TMA = NTHREADS + 32;
+constexpr int NST = 4;                   // A boxes of 128 rows x 32 columns in flight
+constexpr uint32_t RAW_BYTES = TR * 32 * 4;   // 16 KB
 constexpr uint32_t S_PIECE = TR * KP * 2;   // 16 KB
 constexpr uint32_t P_PIECE = TN * KP * 2;   // 32 KB
 constexpr uint32_t IDESC = idesc_bf16(TR, TN, 0);
 
-enum { B_SF0 = 0, B_SF1, B_SE0, B_SE1, B_DF0, B_DF1, B_DE0, B_DE1, B_DONE, NBAR };
+enum { B_SF0 = 0, B_SF1, B_SE0, B_SE1, B_DF0, B_DF1, B_DE0, B_DE1, B_DONE, B_RF0,
+       B_RE0 = B_RF0 + NST, NBAR = B_RE0 + NST };
 
 // Optional timeline of CTA 0, compiled only when IDSK_RC_TRACE is defined by a
 // profiling harness.
@@ -101,15 +113,22 @@ __device__ __forceinline__ void split3(double x, uint16_t& p0, uint16_t& p1, uin
   p2 = *reinterpret_cast<const uint16_t*>(&h2);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+// TMA: A(R, C) reaches the epilogue through an NST-stage ring of TMA boxes
+// (producer warp 13) and the skeleton pieces are single-buffered to make room;
+// otherwise the epilogue loads A itself and the pieces are double-buffered.
+template <bool TMA>
+__global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     recon_tc_kernel(const float* __restrict__ A, int64_t lda, int64_t m, int n,
                     const int* __restrict__ J, const double* __restrict__ P, int k,
-                    double* __restrict__ part, int* __restrict__ status, InterpGeom geo) {
+                    double* __restrict__ part, int* __restrict__ status, InterpGeom geo,
+                    const __grid_constant__ CUtensorMap tmap) {
+  constexpr int NSB = TMA ? 1 : 2;                 // skeleton piece buffers
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t s_p = base;                       // P pieces: 3 x 32 KB
-  const uint32_t s_s = s_p + 3u * P_PIECE;         // S pieces: 2 buffers x 3 x 16 KB
-  const uint32_t bars = s_s + 2u * 3u * S_PIECE;
+  const uint32_t s_s = s_p + 3u * P_PIECE;         // S pieces: NSB buffers x 3 x 16 KB
+  const uint32_t s_raw = s_s + (uint32_t)NSB * 3u * S_PIECE;   // TMA: NST x 16 KB
+  const uint32_t bars = s_raw + (TMA ? NST * RAW_BYTES : 0u);
   const uint32_t tmem_slot = bars + NBAR * 8u;
   const uint32_t abort_flag = tmem_slot + 4u;
   __shared__ int Js[kRecKMax];
@@ -136,6 +155,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_init(bar(B_DE0), NEPI);
     mbar_init(bar(B_DE1), NEPI);
     mbar_init(bar(B_DONE), 1);
+    if (TMA) {
+      for (int q = 0; q < NST; ++q) {
+        mbar_init(bar(B_RF0 + q), 1);
+        mbar_init(bar(B_RE0 + q), NEPI / 2);   // the 4 warps of one column half
+      }
+    }
     st_volatile_shared(abort_flag, 0);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -187,7 +212,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int cb = c0 + ch * 128 + c4 * 32;
         const bool full = rok && (cb + 31 < n);
         float v[32];
-        if (full) {
+        if constexpr (TMA) {
+          // box u of the ring sequence: row block i, column half ch, chunk c4
+          // (zero-filled outside the matrix)
+          const int u = i * 8 + 2 * c4 + ch, st = u % NST;
+          if (!mbar_wait(bar(B_RF0 + st), (u / NST) & 1, abort_flag, 64)) {
+            ok = false;
+            break;
+          }
+          const float* box =
+              reinterpret_cast<const float*>(smem_raw + (s_raw - smem_u32(smem_raw))) +
+              st * (RAW_BYTES / 4) + q * 32 + lane;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = box[j * TR];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_RE0 + st));
+        } else if (full) {
           const float* p = A + r + (int64_t)cb * lda;
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = __ldcs(p + (int64_t)j * lda);
@@ -249,7 +289,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int rl = tid - NEPI * 32;          // row of the block owned by this thread
     uint8_t* sm_gen = smem_raw + (s_s - smem_u32(smem_raw));
     for (int i = 0; i < nloc; ++i) {
-      const int b = i & 1;
+      const int b = i % NSB, use = i / NSB;
       const int64_t r = (rb_begin + i) * TR + rl;
       const bool rok = r < m;
       float x[KP];
@@ -280,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
-      if (i >= 2 && !mbar_wait(bar(B_SE0 + b), ((i >> 1) - 1) & 1, abort_flag, 64)) break;
+      if (use >= 1 && !mbar_wait(bar(B_SE0 + b), (use - 1) & 1, abort_flag, 64)) break;
       uint8_t* sbp = sm_gen + (size_t)b * 3u * S_PIECE;
 #pragma unroll
       for (int t0 = 0; t0 < KP; t0 += 8) {
@@ -305,15 +345,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0) mbar_arrive(bar(B_SF0 + b));
       if (rl == 0) RC_TRACE(1, i);
     }
-  } else if (lane == 0) {
+  } else if (warp == MMA_WARP && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     for (int i = 0; i < nloc; ++i) {
-      const int b = i & 1;
-      if (!mbar_wait(bar(B_SF0 + b), (i >> 1) & 1, abort_flag, 64)) break;
+      const int b = i & 1;                  // TMEM accumulator
+      const int sbuf = i % NSB, suse = i / NSB;   // skeleton piece buffer
+      if (!mbar_wait(bar(B_SF0 + sbuf), suse & 1, abort_flag, 64)) break;
       if (i >= 2 && !mbar_wait(bar(B_DE0 + b), ((i >> 1) - 1) & 1, abort_flag, 64)) break;
       tc_fence_after();
       RC_TRACE(2, i);
-      const uint32_t sb = s_s + (uint32_t)b * 3u * S_PIECE;
+      const uint32_t sb = s_s + (uint32_t)sbuf * 3u * S_PIECE;
       const uint32_t d = tmem + (uint32_t)(b * TN);
       for (int kk = 0; kk < KP / 16; ++kk) {
 #pragma unroll
@@ -325,7 +366,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       mma_commit(bar(B_DF0 + b));
-      mma_commit(bar(B_SE0 + b));
+      mma_commit(bar(B_SE0 + sbuf));
     }
     mma_commit(bar(B_DONE));
     const long long t0 = clock64();
@@ -333,6 +374,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (clock64() - t0 > kWaitCycles) {
         st_volatile_shared(abort_flag, 1);
         break;
+      }
+    }
+  } else if (TMA && warp == PROD_WARP && lane == 0) {
+    // ------------------------------------------------------- TMA producer
+    const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
+    const uint64_t once = policy_evict_first();
+    int u = 0;
+    bool ok = true;
+    for (int i = 0; i < nloc && ok; ++i) {
+      const int row = (int)((rb_begin + i) * TR);
+      for (int bi = 0; bi < 8; ++bi, ++u) {   // chunk c4 = bi / 2 of column half bi % 2
+        const int st = u % NST;
+        if (u >= NST && !mbar_wait(bar(B_RE0 + st), ((u / NST) - 1) & 1, abort_flag, 32)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(bar(B_RF0 + st), RAW_BYTES);
+        tma_load_2d(s_raw + (uint32_t)st * RAW_BYTES, tm, row, c0 + (bi & 1) * 128 + (bi >> 1) * 32,
+                    bar(B_RF0 + st), once);
       }
     }
   }
@@ -368,13 +428,19 @@ int recon_tc_grid(int64_t m, int64_t n, int nsm) {
 cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, const int* J,
                             const double* P, int k, double* part, int grid, int* status,
                             cudaStream_t st, KernelTimer* timer, const InterpGeom* interp) {
-  const size_t sm = 1024 + 3u * P_PIECE + 6u * S_PIECE + NBAR * 8 + 16;
-  cudaError_t e = cudaFuncSetAttribute(recon_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  const char* env = getenv("IDSKETCH_RECON_TMA");
+  const bool tma = !(env && env[0] == '0') && make_tmap_f32_2d(A, m, n, lda, TR, 32, &tm);
+  const size_t sm = 1024 + 3u * P_PIECE + (tma ? 3u * S_PIECE + NST * RAW_BYTES : 6u * S_PIECE) +
+                    NBAR * 8 + 16;
+  auto kern = tma ? recon_tc_kernel<true> : recon_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
   const InterpGeom geo = interp ? *interp : InterpGeom{};
-  recon_tc_kernel<<<grid, NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status, geo);
+  kern<<<grid, tma ? NTHREADS_TMA : NTHREADS, sm, st>>>(A, lda, m, (int)n, J, P, k, part, status,
+                                                         geo, tm);
   count_launches(1);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (timer) e = timer->mark(st);

@@ -98,34 +98,6 @@ struct Smem {
   uint32_t abort_flag;
 };
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-// L2 policies: A streams through once (evict first); the per-CTA W^T slabs
-// are read-modify-written every few row blocks and should stay in L2.
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-// 2D tiled TMA load of one box (x = row, y = column) into shared memory.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, int y,
-                                            uint32_t bar, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-      "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(policy)
-      : "memory");
-}
-
 __device__ __forceinline__ void st_f64_hint(double* p, double v, uint64_t policy) {
   asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
                : "memory");
@@ -667,46 +639,13 @@ size_t tc_smem_bytes() {
          2u * PSI_BYTES + (TMA ? NST * RAW_BYTES + TR * 8u : 0u) + NBAR * 8 + 16;
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
 // Tensor map of the window's single segment: rows x columns FP32, boxes of
 // 128 rows x 32 columns, zero fill outside.  False when it cannot be built.
 bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
-  if (w.nseg != 1 || (((uintptr_t)w.seg[0].ptr) & 15u) != 0 || (w.seg[0].ld & 3) != 0)
-    return false;
+  if (w.nseg != 1) return false;
   const char* env = getenv("IDSKETCH_SKETCH_TMA");
   if (env && env[0] == '0') return false;
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)a.m, (cuuint64_t)w.seg[0].ncols};
-  const cuuint64_t strides[1] = {(cuuint64_t)w.seg[0].ld * 4u};
-  const cuuint32_t box[2] = {(cuuint32_t)TR, 32u};
-  const cuuint32_t es[2] = {1u, 1u};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(w.seg[0].ptr), dims,
-             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+  return make_tmap_f32_2d(w.seg[0].ptr, a.m, w.seg[0].ncols, w.seg[0].ld, TR, 32, tm);
 }
 
 template <int NP, bool TMA>
