@@ -313,17 +313,17 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS, 1)
 }
 
 // P(:, j) for every column j: e_u when j = J[u]; otherwise the solution of
-// R11 x = R(:, j) by back-substitution, R11(t, u) = R(t, J[u]).  R11 and the
-// solution vectors of the block's columns live in shared memory.
-constexpr int SP_THREADS = 64;
-constexpr int SP_LD = kLMax + 1;   // odd stride: per-thread rows on distinct banks
-__global__ void __launch_bounds__(SP_THREADS) solve_p_kernel(
+// R11 x = R(:, j) by back-substitution, R11(t, u) = R(t, J[u]).  One warp per
+// column, column-oriented: x_t = b_t / R11(t, t) (by the diagonal's
+// reciprocal, formed once per block), then b_u -= R11(u, t) x_t
+// for u < t, lane u holding b_u and b_{u+32}.  R11 lives in shared memory.
+constexpr int SP_WARPS = 8;
+__global__ void __launch_bounds__(SP_WARPS * 32) solve_p_kernel(
     const double* __restrict__ R, const int* __restrict__ J, const int* __restrict__ colpos,
     const int* __restrict__ kout, int k, int n, double* __restrict__ P) {
-  extern __shared__ double sm[];
-  double* xs = sm;                              // [SP_THREADS][SP_LD]
-  double* r11 = sm + SP_THREADS * SP_LD;        // kk x kk
+  extern __shared__ double r11[];   // kk x kk, row-major
   __shared__ int Js[kLMax];
+  __shared__ double rdiag[kLMax];   // 1 / R11(t, t)
   const int kk = *kout;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) Js[e] = J[e];
   __syncthreads();
@@ -332,20 +332,33 @@ __global__ void __launch_bounds__(SP_THREADS) solve_p_kernel(
     r11[e] = R[(int64_t)tt * n + Js[u]];
   }
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) rdiag[e] = 1.0 / r11[e * kk + e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * SP_WARPS + (threadIdx.x >> 5);
   if (j >= n) return;
   const int cp = colpos[j];
   if (cp >= 0) {
-    for (int tt = 0; tt < k; ++tt) P[(int64_t)tt * n + j] = (tt == cp) ? 1.0 : 0.0;
+    for (int tt = lane; tt < k; tt += 32) P[(int64_t)tt * n + j] = (tt == cp) ? 1.0 : 0.0;
     return;
   }
-  double* x = xs + threadIdx.x * SP_LD;
+  double b0 = lane < kk ? R[(int64_t)lane * n + j] : 0.0;
+  double b1 = lane + 32 < kk ? R[(int64_t)(lane + 32) * n + j] : 0.0;
   for (int tt = kk - 1; tt >= 0; --tt) {
-    double v = R[(int64_t)tt * n + j];
-    for (int u = tt + 1; u < kk; ++u) v -= r11[tt * kk + u] * x[u];
-    x[tt] = v / r11[tt * kk + tt];
+    const double bt = __shfl_sync(0xffffffffu, tt < 32 ? b0 : b1, tt & 31);
+    const double xt = bt * rdiag[tt];
+    if (lane == (tt & 31)) {
+      if (tt < 32)
+        b0 = xt;
+      else
+        b1 = xt;
+    }
+    if (lane < tt) b0 -= r11[lane * kk + tt] * xt;
+    if (lane + 32 < tt) b1 -= r11[(lane + 32) * kk + tt] * xt;
   }
-  for (int tt = 0; tt < k; ++tt) P[(int64_t)tt * n + j] = tt < kk ? x[tt] : 0.0;
+  // lane tt & 31 holds x_tt (in b0 for tt < 32, in b1 otherwise); rows past k_out are 0
+  for (int tt = lane; tt < k; tt += 32)
+    P[(int64_t)tt * n + j] = tt < kk ? (tt < 32 ? b0 : b1) : 0.0;
 }
 
 }  // namespace
@@ -364,14 +377,14 @@ cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double 
 
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
                            int k, int n, double* P, cudaStream_t st) {
-  const size_t sm = sizeof(double) * ((size_t)SP_THREADS * SP_LD + (size_t)k * k);
+  const size_t sm = sizeof(double) * (size_t)k * k;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(solve_p_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  solve_p_kernel<<<(n + SP_THREADS - 1) / SP_THREADS, SP_THREADS, sm, st>>>(R, J, colpos, kout,
-                                                                           k, n, P);
+  solve_p_kernel<<<(n + SP_WARPS - 1) / SP_WARPS, SP_WARPS * 32, sm, st>>>(R, J, colpos, kout, k,
+                                                                         n, P);
   count_launches(1);
   return cudaGetLastError();
 }
