@@ -15,15 +15,18 @@
 // residual norm, ties to the lowest index; pivoting stops below the rank
 // tolerance.
 //
-// Pass structure (three launches per step).  A^T v_s = A(s, :)^T +
+// Pass structure (four launches per step).  A^T v_s = A(s, :)^T +
 // (A^T u below row s) / (u_s - beta), so the one O(m_c n) product per step
-// needs u only, not the Householder scalars: step_kernel forms u for its rows
-// and, in the same pass over A_c, the row-range partials of A^T u, V^T u and
-// ||u||^2; the last of its CTAs to finish sums the partials of the scalars.
-// finalize_kernel sums the partials of A^T u per column and updates F, R and
-// the norms; recompute_kernel refreshes flagged norms, and its last CTA picks
-// the next pivot.  Every sum runs in a fixed order (CTA-ordered partials), so
-// results do not depend on scheduling.
+// needs u only, not the Householder scalars:
+//   step_kernel        every CTA finds the step's pivot from the norms, forms
+//                      u for its rows and the partials of V^T u and ||u||^2;
+//                      the last CTA to finish sums them into the scalars;
+//   stream_gemv_kernel A_c^T u (or gemv_kernel when A_c cannot be streamed);
+//   finalize_kernel    sums the A_c^T u partials per column, updates F, R and
+//                      the norms, flags norms that lost too many bits;
+//   recompute_kernel   recomputes the flagged norms (usually none).
+// Every sum runs in a fixed order (CTA-ordered partials), so results do not
+// depend on scheduling.
 //
 // Precision: the O(m_c n) product A_c^T u and the O(m_c s) work of each
 // step (u, V_s^T u, ||u||^2, the reflectors V themselves) run on the FP32
@@ -45,8 +48,7 @@ namespace {
 
 constexpr double kRecomputeFrac = 1.0 / (1 << 20);
 // cint layout
-constexpr int CI_P = 0, CI_STOP = 1, CI_NREC = 2, CI_KOUT = 3, CI_CNT_STEP = 4, CI_CNT_REC = 5,
-              CI_CNT_FIN = 6, CI_PICKED = 7;
+constexpr int CI_P = 0, CI_STOP = 1, CI_NREC = 2, CI_KOUT = 3, CI_CNT_STEP = 4;
 // cscal layout
 constexpr int CS_ALPHA = 0, CS_SIGMA = 1, CS_BETA = 2, CS_TAU = 3, CS_DEN = 4, CS_TOL = 5;
 
@@ -75,26 +77,29 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
-// Pivot of step s over the columns not yet pivoted: largest residual norm
-// (compared as squared norms, which orders the same way), ties to the lowest
-// index.  A non-negative double orders like its IEEE bit pattern read as an
-// unsigned integer, so the comparisons run on the integer units (negative
-// downdated values count as zero).  Whole block; thread 0 records the
-// outcome.
+// Pivot of step s over the columns not pivoted at steps 0..s-1: largest
+// residual norm (compared as squared norms, which orders the same way), ties
+// to the lowest index.  A non-negative double orders like its IEEE bit pattern
+// read as an unsigned integer, so the comparisons run on the integer units
+// (negative downdated values count as zero).  Whole block; every block of a
+// grid may run it on the same norms and gets the same pivot (-1: stop below
+// the rank tolerance); the writer block records it.
 __device__ __forceinline__ unsigned long long norm_key(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   return (b >> 63) ? 0ull : b;
 }
 
-__device__ void pick_pivot(const double* __restrict__ nu2, int n, int s, int* __restrict__ colpos,
-                           int* __restrict__ Jc, const double* __restrict__ cscal,
-                           int* __restrict__ cint) {
+__device__ int pick_pivot(const double* __restrict__ nu2, int n, int s, int* __restrict__ colpos,
+                          int* __restrict__ Jc, const double* __restrict__ cscal,
+                          int* __restrict__ cint, bool writer) {
   __shared__ unsigned long long bv[32];
   __shared__ int bi[32];
+  __shared__ int chosen;
   unsigned long long v = 0ull;
   int idx = 0x7fffffff;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    if (colpos[j] >= 0) continue;
+    const int cp = colpos[j];
+    if (cp >= 0 && cp < s) continue;   // pivoted at an earlier step
     const unsigned long long key = norm_key(nu2[j]);
     if (idx == 0x7fffffff || key > v) {   // j increases within a thread: strict >
       v = key;
@@ -127,15 +132,21 @@ __device__ void pick_pivot(const double* __restrict__ nu2, int n, int s, int* __
       }
     }
     const double tol = cscal[CS_TOL];
-    if (p == 0x7fffffff || !(b > norm_key(tol * tol))) {
-      cint[CI_STOP] = 1;
-      cint[CI_KOUT] = s;
-    } else {
-      cint[CI_P] = p;
-      Jc[s] = p;
-      colpos[p] = s;
+    const bool stop = p == 0x7fffffff || !(b > norm_key(tol * tol));
+    chosen = stop ? -1 : p;
+    if (writer) {
+      if (stop) {
+        cint[CI_STOP] = 1;
+        cint[CI_KOUT] = s;
+      } else {
+        cint[CI_P] = p;
+        Jc[s] = p;
+        colpos[p] = s;
+      }
     }
   }
+  __syncthreads();
+  return chosen;
 }
 
 template <typename T>
@@ -157,11 +168,9 @@ __global__ void init_norms_kernel(const T* __restrict__ Ac, int64_t mc, int n,
   }
 }
 
-// Rank tolerance, counters, and the pivot of step 0.
-__global__ void init_tol_kernel(const double* __restrict__ nu20, int n, int kmax,
-                                double tol_factor, int* __restrict__ colpos,
-                                int* __restrict__ Jc, double* __restrict__ cscal,
-                                int* __restrict__ cint) {
+// Rank tolerance and counters.
+__global__ void init_tol_kernel(const double* __restrict__ nu20, int n, double tol_factor,
+                                double* __restrict__ cscal, int* __restrict__ cint) {
   __shared__ double sh[33];
   double ss = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) ss += nu20[j];
@@ -173,12 +182,8 @@ __global__ void init_tol_kernel(const double* __restrict__ nu20, int n, int kmax
     cint[CI_NREC] = 0;
     cint[CI_KOUT] = 0;
     cint[CI_CNT_STEP] = 0;
-    cint[CI_CNT_REC] = 0;
-    cint[CI_CNT_FIN] = 0;
-    cint[CI_PICKED] = 0;
+
   }
-  __syncthreads();
-  if (kmax > 0) pick_pivot(nu20, n, 0, colpos, Jc, cscal, cint);
 }
 
 // True in every thread of the one CTA that finished last (release/acquire
@@ -210,13 +215,16 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
     float2* __restrict__ V, const double* __restrict__ F, int64_t ldf,
     float* __restrict__ uh, float* __restrict__ ul, double* __restrict__ hpart,
     double* __restrict__ hvec, double* __restrict__ Rc, double* __restrict__ cscal,
+    const double* __restrict__ nu2, int* __restrict__ colpos, int* __restrict__ Jc,
     int* __restrict__ cint) {
   __shared__ float2 fp[kLMax];
   __shared__ float2 ud[ST_THREADS];
   if (cint[CI_STOP]) return;
-  const int p = cint[CI_P];
+  // pivot of this step, found by every CTA from the final norms of step s-1
+  const int p = pick_pivot(nu2, n, s, colpos, Jc, cscal, cint, blockIdx.x == 0);
+  if (p < 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (blockIdx.x == 0 && tid == 0) cint[CI_PICKED] = 0;   // read by this step's recompute
+  if (blockIdx.x == 0 && tid == 0) cint[CI_NREC] = 0;   // appended to by this step's finalize
   for (int t = tid; t < s; t += ST_THREADS) fp[t] = df_of(F[(int64_t)t * ldf + p]);
   const double psig = s > 0 ? cscal[CS_SIGMA] : 0.0;
   const float2 prcp = df_of((s > 0 && psig != 0.0) ? 1.0 / cscal[CS_DEN] : 0.0);   // v = u / den
@@ -679,9 +687,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) finalize_kernel(
     const T* __restrict__ Ac, int64_t mc, int n, int s, int G, const float2* __restrict__ V,
     double* __restrict__ F, int64_t ldf, const double* __restrict__ gpart,
-    const double* __restrict__ hvec, int* __restrict__ colpos, double* __restrict__ Rc,
+    const double* __restrict__ hvec, const int* __restrict__ colpos, double* __restrict__ Rc,
     double* __restrict__ nu2, const double* __restrict__ nu20, int* __restrict__ rlist,
-    int kmax, int* __restrict__ Jc, const double* __restrict__ cscal, int* __restrict__ cint) {
+    const double* __restrict__ cscal, int* __restrict__ cint) {
   __shared__ double part[8][FIN_COLS];
   __shared__ double pfh[8][FIN_COLS];
   __shared__ double prr[8][FIN_COLS];
@@ -762,28 +770,22 @@ __global__ void __launch_bounds__(256) finalize_kernel(
       }
     }
   }
-  // the last CTA picks the next pivot unless a norm needs recomputing first
-  if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_FIN))) return;
-  if (cint[CI_NREC] != 0) return;
-  if (s + 1 < kmax) pick_pivot(nu2, n, s + 1, colpos, Jc, cscal, cint);
-  if (tid == 0) cint[CI_PICKED] = 1;
 }
 
-// nu_j^2 = ||A^(s+1)(s+1:, j)||^2 from the definition, for the flagged
-// columns (column s of V still holds u: v_s = u / den below row s); the last
-// CTA then picks the pivot of step s + 1.
+// nu_j^2 = ||A^(s+1)(s+1:, j)||^2 from the definition, for the columns that
+// finalize_kernel flagged (column s of V still holds u: v_s = u / den below
+// row s).  Usually there are none and every CTA returns at once.
 template <typename T>
-__global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int n, int s, int kmax,
+__global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int s,
                                  const float2* __restrict__ V, const double* __restrict__ F,
                                  int64_t ldf, const int* __restrict__ rlist,
                                  double* __restrict__ nu2, double* __restrict__ nu20,
-                                 int* __restrict__ colpos, int* __restrict__ Jc,
-                                 const double* __restrict__ cscal, int* __restrict__ cint) {
+                                 const double* __restrict__ cscal, const int* __restrict__ cint) {
   __shared__ double fj[kLMax + 1];
   __shared__ double sh[33];
   if (cint[CI_STOP]) return;
-  if (cint[CI_PICKED]) return;   // finalize_kernel found nothing to recompute and picked
   const int nrec = cint[CI_NREC];
+  if (nrec == 0) return;
   const double sigma = cscal[CS_SIGMA];
   const double rden = sigma != 0.0 ? 1.0 / cscal[CS_DEN] : 0.0;
   for (int idx = blockIdx.x; idx < nrec; idx += gridDim.x) {
@@ -805,9 +807,6 @@ __global__ void recompute_kernel(const T* __restrict__ Ac, int64_t mc, int n, in
       nu20[j] = ss;
     }
   }
-  if (!last_cta(reinterpret_cast<unsigned*>(cint + CI_CNT_REC))) return;
-  if (threadIdx.x == 0) cint[CI_NREC] = 0;
-  if (s + 1 < kmax) pick_pivot(nu2, n, s + 1, colpos, Jc, cscal, cint);
 }
 
 __global__ void coarse_done_kernel(int kmax, int k, int* __restrict__ Jc, int* __restrict__ cint) {
@@ -874,15 +873,15 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   } else {
     init_norms_kernel<T><<<n, 256, 0, st>>>(Ac, mc, n, h->d_nu2, h->d_nu20, h->d_colposc);
   }
-  init_tol_kernel<<<1, 1024, 0, st>>>(h->d_nu20, n, kmax, ID_RANK_TOL_FACTOR, h->d_colposc,
-                                      h->d_Jc, h->d_cscal, h->d_cint);
+  init_tol_kernel<<<1, 1024, 0, st>>>(h->d_nu20, n, ID_RANK_TOL_FACTOR, h->d_cscal, h->d_cint);
   count_launches(2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int s = 0; s < kmax; ++s) {
     step_kernel<T><<<G, ST_THREADS, 0, st>>>(Ac, mc, n, s, rpc, V2, h->d_F, ldf, h->d_vh,
                                              h->d_vl, h->d_upart, h->d_hvec, h->d_Rc,
-                                             h->d_cscal, h->d_cint);
+                                             h->d_cscal, h->d_nu2, h->d_colposc, h->d_Jc,
+                                             h->d_cint);
     if (streamed)
       stream_gemv_kernel<<<SG, SG_THREADS, sg_smem, st>>>(
           reinterpret_cast<const float*>(Ac), mc, n, 0, h->d_vh, h->d_vl, h->d_gvec,
@@ -892,11 +891,9 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
                                                           h->d_vl, h->d_gvec, h->d_cint);
     finalize_kernel<T><<<fin_blocks, 256, 0, st>>>(
         Ac, mc, n, s, streamed ? -SG : RS, V2, h->d_F, ldf, h->d_gvec, h->d_hvec,
-        h->d_colposc, h->d_Rc, h->d_nu2, h->d_nu20, h->d_rlist, kmax, h->d_Jc, h->d_cscal,
-        h->d_cint);
-    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, n, s, kmax, V2, h->d_F, ldf, h->d_rlist,
-                                            h->d_nu2, h->d_nu20, h->d_colposc, h->d_Jc,
-                                            h->d_cscal, h->d_cint);
+        h->d_colposc, h->d_Rc, h->d_nu2, h->d_nu20, h->d_rlist, h->d_cscal, h->d_cint);
+    recompute_kernel<T><<<64, 256, 0, st>>>(Ac, mc, s, V2, h->d_F, ldf, h->d_rlist, h->d_nu2,
+                                            h->d_nu20, h->d_cscal, h->d_cint);
     count_launches(4);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -25,7 +25,7 @@
 //   warp 13     (TMA form) streams A(R, C) in boxes of 128 rows x 32 columns
 //               through a 4-stage shared-memory ring for the epilogue
 // At most 4 warps per SM sub-partition (128 registers each).  The TMA form
-// (A 16-byte aligned, lda a multiple of 4) keeps 64 KB of A in flight per SM
+// (A 16-byte aligned, lda a multiple of 4) keeps 80 KB of A in flight per SM
 // and single-buffers the skeleton pieces to make room; the other form loads
 // A in the epilogue warps directly.
 // Waits are bounded as in the sketch kernel; on timeout the status word is
@@ -53,7 +53,7 @@ constexpr int MMA_WARP = NEPI + NGAT;    // 12
 constexpr int NTHREADS = (NEPI + NGAT + 1) * 32;
 constexpr int PROD_WARP = MMA_WARP + 1;  // TMA producer (TMA form only)
 constexpr int NTHREADS_TMA = NTHREADS + 32;
-constexpr int NST = 4;                   // A boxes of 128 rows x 32 columns in flight
+constexpr int NST = 5;                   // A boxes of 128 rows x 32 columns in flight
 constexpr uint32_t RAW_BYTES = TR * 32 * 4;   // 16 KB
 constexpr uint32_t S_PIECE = TR * KP * 2;   // 16 KB
 constexpr uint32_t P_PIECE = TN * KP * 2;   // 32 KB
@@ -97,17 +97,6 @@ __device__ __forceinline__ void split3(float x, uint16_t& p0, uint16_t& p1, uint
   const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
   const float r2 = r1 - __bfloat162float(h1);
   const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
-  p0 = *reinterpret_cast<const uint16_t*>(&h0);
-  p1 = *reinterpret_cast<const uint16_t*>(&h1);
-  p2 = *reinterpret_cast<const uint16_t*>(&h2);
-}
-
-__device__ __forceinline__ void split3(double x, uint16_t& p0, uint16_t& p1, uint16_t& p2) {
-  const __nv_bfloat16 h0 = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(h0);
-  const __nv_bfloat16 h1 = __double2bfloat16(r1);
-  const double r2 = r1 - (double)__bfloat162float(h1);
-  const __nv_bfloat16 h2 = __double2bfloat16(r2);
   p0 = *reinterpret_cast<const uint16_t*>(&h0);
   p1 = *reinterpret_cast<const uint16_t*>(&h1);
   p2 = *reinterpret_cast<const uint16_t*>(&h2);
@@ -170,8 +159,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     const int c = e / KP, t = e % KP;
     double v = 0.0;
     if (t < k && c0 + c < n) v = P[(int64_t)t * n + c0 + c];
+    // the three 8-bit pieces hold 24 bits: split the FP32 rounding of P on
+    // the FP32 units (the FP64 split cost a sizeable share of a launch)
     uint16_t p0, p1, p2;
-    split3(v, p0, p1, p2);
+    split3((float)v, p0, p1, p2);
     const uint32_t off = swz((uint32_t)c, (uint32_t)t, 1024u);
     st_shared_u16(s_p + off, p0);
     st_shared_u16(s_p + P_PIECE + off, p1);
