@@ -509,14 +509,6 @@ constexpr uint32_t SG_COLB = SG_ROWS * 4;                  // 16 KB column piece
 constexpr uint32_t SG_STAGE = (SG_COLS + 2) * SG_COLB;     // + uh, ul
 constexpr int SG_THREADS = (SG_CONS + 1) * 32;
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
 __device__ __forceinline__ void mbar_expect_tx_arrive(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
@@ -538,7 +530,7 @@ __host__ __device__ inline void stream_cta_range(int64_t T, int G, int64_t nchun
 __global__ void __launch_bounds__(SG_THREADS, 1) stream_gemv_kernel(
     const float* __restrict__ Ac, int64_t mc, int n, int mode, const float* __restrict__ uh,
     const float* __restrict__ ul, double* __restrict__ part, int* __restrict__ status,
-    const int* __restrict__ cint) {
+    const int* __restrict__ cint, int64_t keep_rows) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * SG_ST];
   __shared__ int abort_flag;
@@ -565,6 +557,9 @@ __global__ void __launch_bounds__(SG_THREADS, 1) stream_gemv_kernel(
   if (warp == SG_CONS) {
     // ---------------------------------------------------------- producer
     if (lane == 0) {
+      // rows [0, keep_rows) of every column stay in L2 from one pass to the
+      // next (evict_last); the rest streams through (evict_first)
+      const uint64_t pol_keep = tc::policy_evict_last(), pol_stream = tc::policy_evict_first();
       int u = 0;
       for (int64_t it = it0; it < it1; ++it, ++u) {
         const int st = u % SG_ST;
@@ -576,12 +571,14 @@ __global__ void __launch_bounds__(SG_THREADS, 1) stream_gemv_kernel(
         const int ncols = n - g * SG_COLS < SG_COLS ? n - g * SG_COLS : SG_COLS;
         const uint32_t dst = base + (uint32_t)st * SG_STAGE;
         mbar_expect_tx_arrive(full0 + 8u * st, bytes * (ncols + (mode == 0 ? 2 : 0)));
+        const uint64_t pol = r0 < keep_rows ? pol_keep : pol_stream;
         for (int q = 0; q < ncols; ++q)
-          bulk_g2s(dst + q * SG_COLB, Ac + (int64_t)(g * SG_COLS + q) * mc + r0, bytes,
-                   full0 + 8u * st);
+          tc::bulk_g2s_hint(dst + q * SG_COLB, Ac + (int64_t)(g * SG_COLS + q) * mc + r0, bytes,
+                            full0 + 8u * st, pol);
         if (mode == 0) {
-          bulk_g2s(dst + SG_COLS * SG_COLB, uh + r0, bytes, full0 + 8u * st);
-          bulk_g2s(dst + (SG_COLS + 1) * SG_COLB, ul + r0, bytes, full0 + 8u * st);
+          tc::bulk_g2s_hint(dst + SG_COLS * SG_COLB, uh + r0, bytes, full0 + 8u * st, pol_keep);
+          tc::bulk_g2s_hint(dst + (SG_COLS + 1) * SG_COLB, ul + r0, bytes, full0 + 8u * st,
+                            pol_keep);
         }
       }
     }
@@ -860,6 +857,16 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
   const bool streamed = vec && getenv("IDSKETCH_COARSE_STREAM") == nullptr;
   const int SG = h->nsm;
   const size_t sg_smem = 128 + (size_t)SG_ST * SG_STAGE;
+  // the leading rows of A_c that stay in L2 between the k passes: about 3/8
+  // of L2 (the rest holds V, u and the partials), whole 4096-row chunks
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev) != cudaSuccess) {
+    cudaGetLastError();
+    l2 = 0;
+  }
+  const double keep_target = 0.375 * (double)l2 / (4.0 * (double)n);
+  const int64_t keep_rows =
+      std::min<int64_t>(mc, (int64_t)(keep_target / SG_ROWS + 0.5) * SG_ROWS);
   if (streamed) {
     cudaError_t e0 = cudaFuncSetAttribute(stream_gemv_kernel,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -867,7 +874,7 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
     if (e0 != cudaSuccess) return e0;
     stream_gemv_kernel<<<SG, SG_THREADS, sg_smem, st>>>(
         reinterpret_cast<const float*>(Ac), mc, n, 1, nullptr, nullptr, h->d_gvec, h->d_status,
-        h->d_cint);
+        h->d_cint, keep_rows);
     norms_from_parts_kernel<<<(n + 255) / 256, 256, 0, st>>>(h->d_gvec, mc, n, SG, h->d_nu2,
                                                              h->d_nu20, h->d_colposc);
   } else {
@@ -885,7 +892,7 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
     if (streamed)
       stream_gemv_kernel<<<SG, SG_THREADS, sg_smem, st>>>(
           reinterpret_cast<const float*>(Ac), mc, n, 0, h->d_vh, h->d_vl, h->d_gvec,
-          h->d_status, h->d_cint);
+          h->d_status, h->d_cint, keep_rows);
     else
       gemv_kernel<T><<<ngroups * RS, GV_THREADS, 0, st>>>(Ac, mc, n, s, chunk, vec, h->d_vh,
                                                           h->d_vl, h->d_gvec, h->d_cint);
