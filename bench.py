@@ -397,6 +397,94 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------ batched form
+
+def batched_problems(count=64, seed=1):
+    """Sizes of the batched workload: 64 channel fields of uneven size, m ~
+    U[50k, 2M] rounded to 3 nx ny nz with nx = nz = 2 ny, n ~ U[64, 512],
+    k ~ U[10, 54] (l = k + 10 <= 64, the library's sketch width), seeds 1..64,
+    FP32 data, every other problem in the BF16 sketch form."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        ny = max(2, int(round((rng.uniform(50_000, 2_000_000) / 12.0) ** (1.0 / 3.0))))
+        n = int(rng.integers(64, 513))
+        k = int(rng.integers(10, 55))
+        out.append(dict(grid=(2 * ny, ny, 2 * ny), n=n, k=k, l=k + 10, seed=b + 1,
+                        prec="bf16" if b % 2 else "exact"))
+    return out
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1905_13257_gb300 import IdBatch, load
+    from synthetic import channel_field
+
+    lib = load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    spec = batched_problems()
+    probs, nbytes = [], 0
+    for p in spec:
+        A = channel_field(p["grid"], NCOMP, p["n"], seed=p["seed"], dtype=torch.float32,
+                          device=dev)
+        probs.append(dict(A=A, k=p["k"], l=p["l"], seed=p["seed"], prec=p["prec"]))
+        nbytes += 4 * A.shape[0] * A.shape[1]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    bt = IdBatch(probs, stream=stream)
+    for _ in range(args.warmup):
+        bt.run()
+    bt.wait()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    l0 = lib.id_kernel_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        bt.run()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.id_kernel_launches() - l0
+    clk = clocks.stop()
+    res = bt.wait()
+    ms = t0.elapsed_time(t1) / args.steps
+    gbs = nbytes / (ms / 1e3) / 1e9
+    peak, kind = measured_peaks()
+    ms_ = [A["A"].shape[0] for A in probs]
+    line = {
+        "metric": "batched randomized ID GB/s of snapshot data", "value": gbs, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic channel fields (seeded), resident in HBM",
+        "config": {"workload": "64 channel fields of uneven size in one graph launch: "
+                               "m ~ U[50k, 2M] (3 x 2ny x ny x 2ny), n ~ U[64, 512], "
+                               "k ~ U[10, 54], l = k + 10, seeds 1..64, FP32, "
+                               "every other problem BF16 sketch",
+                   "problems": len(probs), "bytes_per_step": nbytes,
+                   "m_range": [min(ms_), max(ms_)],
+                   "n_range": [min(p["n"] for p in spec), max(p["n"] for p in spec)],
+                   "k_range": [min(p["k"] for p in spec), max(p["k"] for p in spec)],
+                   "l2": f"inputs larger than L2 ({nbytes / 1e9:.1f} GB); no flush needed"},
+        "roofline": {"kernel": "whole batch (one graph launch; sketch, QR, solve)",
+                     "bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": "of " + kind,
+                     "unit": "GB/s", "frac": gbs / peak, "traffic": None},
+        "gpu_launches": launches, "clocks": clk,
+        "k_out_short": sum(1 for (_, _, ko), p in zip(res, spec) if ko < p["k"]),
+    }
+    print(json.dumps(line))
+    bt.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,6 +500,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
                     help="y-planes of component u in the CPU-baseline sample")
+    ap.add_argument("--workload", choices=["channel", "batched64"], default="channel",
+                    help="batched64: the batched form (64 matrices of uneven size)")
     ap.add_argument("--ref-planes", type=int, default=2,
                     help="y-planes per step of the reference arm's sample")
     args = ap.parse_args()
@@ -419,6 +509,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched64":
+        return run_batched(args)
     return run_ours(args)
 
 

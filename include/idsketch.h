@@ -214,6 +214,69 @@ id_status id_single_pass_error(id_sketch* h, const void* d_A, int64_t lda, int64
                                const int32_t* Jc, const double* Pc, int32_t kc, double* rel_fro,
                                double* rel_max);
 
+/* ---------------------------------------------------------------------
+ * Batched form: many independent snapshot matrices, of uneven sizes, each
+ * through the randomized ID (Algorithm 4, Sec. 2.4) in ONE CUDA-graph launch.
+ * This serves the block-wise compression of Sec. 3.3 (a large snapshot
+ * matrix split into column blocks, each compressed on its own) and many
+ * variables or windows compressed side by side.  Problem b draws its own Psi
+ * and Omega from its seed, so its result equals that of one id_sketch handle
+ * with the same m, n, k, l, seed, dtype and prec that streams the whole
+ * matrix and calls id_factor.
+ * ------------------------------------------------------------------- */
+
+/* Largest batch and largest n of one problem of the batched form. */
+#define ID_BATCH_MAX_PROBLEMS 1024
+#define ID_BATCH_MAX_COLS 512
+
+typedef struct {
+  const void* d_A;   /* device, column-major m x n, leading dimension lda;
+                        read at every id_batch_run, caller-owned (the caller
+                        keeps it alive and unchanged while a run is in flight) */
+  int64_t lda;       /* >= m                                                  */
+  int64_t m;         /* rows, >= 1                                            */
+  int32_t n;         /* snapshots, 1 <= n <= ID_BATCH_MAX_COLS                */
+  int32_t k;         /* target rank, 1 <= k <= min(l, n)                      */
+  int32_t l;         /* sketch width, k <= l <= 64                            */
+  int32_t dtype;     /* id_dtype of A                                         */
+  int32_t prec;      /* id_sketch_prec (ID_SKETCH_BF16 for FP32 data only)    */
+  int32_t reserved;  /* must be zero                                          */
+  uint64_t seed;     /* seed of this problem's Psi and Omega                  */
+} id_batch_problem;
+
+typedef struct id_batch id_batch;   /* opaque, library-owned */
+
+/* Create a batch on the current device: copies the problem list, creates one
+ * sketch state per problem and a pool of up to 8 worker streams (problems
+ * are spread over them, largest first, to balance the bytes), and draws each
+ * Omega.  cuda_stream: the stream id_batch_run enqueues on (NULL = legacy
+ * default stream).  Errors: ID_ERR_INVALID_ARG (NULL, count outside
+ * [1, ID_BATCH_MAX_PROBLEMS], a problem out of its ranges), ID_ERR_OOM,
+ * ID_ERR_CUDA. */
+id_status id_batch_create(const id_batch_problem* problems, int32_t count, void* cuda_stream,
+                          id_batch** out);
+
+/* Enqueue the whole batch on the batch's stream: per problem the fused sketch
+ * W = Psi A of all n columns, the pivoted QR of W and the solve for P; no
+ * host synchronisation.  Outputs (device memory, caller-owned):
+ *   J    problem b's k_b pivots at J + sum_{c<b} k_c, pivot order, -1 past k_out
+ *   P    problem b's k_b x n_b FP64 row-major at P + sum_{c<b} k_c n_c
+ *   kout problem b's k_out at kout[b]
+ * The first run (and a run with other output pointers) captures the work
+ * into a CUDA graph, worker streams as parallel branches; later runs replay
+ * it.  Errors: ID_ERR_INVALID_ARG (NULL or host output pointers),
+ * ID_ERR_CUDA (the batch is then poisoned: only destroy is valid). */
+id_status id_batch_run(id_batch* b, int32_t* J, double* P, int32_t* kout);
+
+/* Wait for the last run; kout_host (count entries, may be NULL) receives
+ * every k_out.  Errors: ID_ERR_STATE (no run yet), ID_ERR_TIMEOUT (a device
+ * wait of some problem gave up; poisoned), ID_ERR_RANK_DEFICIENT (some
+ * k_out < k; the outputs are valid for the k_out pivots), ID_ERR_CUDA. */
+id_status id_batch_wait(id_batch* b, int32_t* kout_host);
+
+/* Synchronise the batch's stream and release everything it holds. */
+void id_batch_destroy(id_batch* b);
+
 /* Borrow the device buffers of the sketch (valid until reset/destroy):
  *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])
  *   Y  m x l, dtype, column-major (entry (i, s) at Y[i + s*m]); NULL unless want_Y

@@ -47,6 +47,25 @@ class IdConfig(C.Structure):
     ]
 
 
+ID_BATCH_MAX_PROBLEMS = 1024
+ID_BATCH_MAX_COLS = 512
+
+
+class IdBatchProblem(C.Structure):
+    _fields_ = [
+        ("d_A", C.c_void_p),
+        ("lda", C.c_int64),
+        ("m", C.c_int64),
+        ("n", C.c_int32),
+        ("k", C.c_int32),
+        ("l", C.c_int32),
+        ("dtype", C.c_int32),
+        ("prec", C.c_int32),
+        ("reserved", C.c_int32),
+        ("seed", C.c_uint64),
+    ]
+
+
 # name -> (restype, argtypes); the exported symbol set of include/idsketch.h
 SIGNATURES = {
     "id_sketch_create": (C.c_int, [C.POINTER(IdConfig), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -71,6 +90,11 @@ SIGNATURES = {
     "id_single_pass_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                        C.c_void_p, C.c_void_p, C.c_int32,
                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "id_batch_create": (C.c_int, [C.POINTER(IdBatchProblem), C.c_int32, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    "id_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "id_batch_wait": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "id_batch_destroy": (None, [C.c_void_p]),
     "id_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "id_timing_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),

@@ -198,6 +198,77 @@ class IdSketch:
         return W, Y, Ac
 
 
+class IdBatch:
+    """Many independent snapshot matrices through the randomized ID in one
+    CUDA-graph launch (id_batch_*).
+
+    problems: a list of dicts with ``A`` (an m x n column-major CUDA tensor,
+    FP32 or FP64, n <= 512), ``k``, ``l``, ``seed`` and optionally ``prec``
+    ("exact" or "bf16").  The tensors are read at every run and stay
+    referenced by the batch.
+    """
+
+    def __init__(self, problems, stream=None):
+        self.lib = B.load()
+        self._sh, self.stream = _stream_handle(stream)
+        arr = (B.IdBatchProblem * len(problems))()
+        self._A = []
+        self.shapes = []
+        for i, p in enumerate(problems):
+            A = p["A"]
+            m = A.shape[0]
+            ld = _colmajor(A, m)
+            if not A.is_cuda or A.dtype not in (torch.float32, torch.float64):
+                raise ValueError("A must be an FP32 or FP64 CUDA tensor")
+            q = arr[i]
+            q.d_A, q.lda, q.m, q.n = A.data_ptr(), ld, m, A.shape[1]
+            q.k, q.l, q.seed = int(p["k"]), int(p["l"]), int(p["seed"])
+            q.dtype = B.ID_F64 if A.dtype == torch.float64 else B.ID_F32
+            q.prec = B.ID_SKETCH_BF16 if p.get("prec", "exact") == "bf16" else B.ID_SKETCH_EXACT
+            self._A.append(A)
+            self.shapes.append((int(p["k"]), A.shape[1]))
+        self.count = len(problems)
+        h = C.c_void_p()
+        B.check(self.lib.id_batch_create(arr, self.count, self._sh, C.byref(h)),
+                "id_batch_create")
+        self.h = h
+        dev = self.stream.device
+        nk = sum(k for k, _ in self.shapes)
+        nkn = sum(k * n for k, n in self.shapes)
+        self.J = torch.empty(nk, dtype=torch.int32, device=dev)
+        self.P = torch.empty(nkn, dtype=torch.float64, device=dev)
+        self.kout = torch.empty(self.count, dtype=torch.int32, device=dev)
+
+    def run(self):
+        """Enqueue the whole batch (one graph launch after the first run)."""
+        B.check(self.lib.id_batch_run(self.h, C.c_void_p(self.J.data_ptr()),
+                                      C.c_void_p(self.P.data_ptr()),
+                                      C.c_void_p(self.kout.data_ptr())), "id_batch_run")
+
+    def wait(self):
+        """Wait for the last run: a list of (J_b, P_b, k_out_b), device views."""
+        ko = (C.c_int32 * self.count)()
+        B.check(self.lib.id_batch_wait(self.h, ko), "id_batch_wait",
+                allow=(B.ID_ERR_RANK_DEFICIENT,))
+        out, jo, po = [], 0, 0
+        for b, (k, n) in enumerate(self.shapes):
+            out.append((self.J[jo:jo + k], self.P[po:po + k * n].view(k, n), int(ko[b])))
+            jo += k
+            po += k * n
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.id_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def gaussian_fill(which, seed, first, count, width, device=None, stream=None):
     """The counter-based Gaussian entries (which=1 Psi, 2 Omega) as a (count, width)
     FP32 CUDA tensor: row i holds G(first + i, 0:width)."""

@@ -19,7 +19,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libidsketch.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "sketch_simt.cu", "sketch_tc.cu", "cpqr.cu", "coarse.cu", "recon.cu",
-           "recon_tc.cu", "single_pass.cu", "noalloc.cu", "tma_host.cu", "gauss_table.cpp"]
+           "recon_tc.cu", "single_pass.cu", "noalloc.cu", "tma_host.cu", "batch.cu",
+           "gauss_table.cpp"]
 
 
 def nvcc() -> str:

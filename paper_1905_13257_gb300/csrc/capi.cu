@@ -138,6 +138,10 @@ bool use_tc(const id_sketch* h) {
   return true;
 }
 
+}  // namespace
+
+namespace idsk {
+
 id_status launch_pending(id_sketch* h) {
   while (!h->pend.empty()) {
     Window w;
@@ -195,6 +199,25 @@ id_status launch_pending(id_sketch* h) {
   h->pend_cols = 0;
   return ID_OK;
 }
+
+id_status factor_enqueue(id_sketch* h) {
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  const int64_t n = h->n_seen;
+  if (n == 0) return ID_ERR_STATE;
+  const int k = h->k, l = h->l;
+  IDSK_CUDA(h, cudaMemcpy2DAsync(h->d_work, sizeof(double) * n, h->d_W,
+                                 sizeof(double) * h->n_max, sizeof(double) * n, l,
+                                 cudaMemcpyDeviceToDevice, h->st));
+  IDSK_CUDA(h, launch_cpqr_small(h->d_work, l, (int)n, (int)n, k, ID_RANK_TOL_FACTOR, h->d_R,
+                                 h->d_J, h->d_colpos, h->d_kout, h->st));
+  IDSK_CUDA(h, launch_solve_p(h->d_R, h->d_J, h->d_colpos, h->d_kout, k, (int)n, h->d_P, h->st));
+  return ID_OK;
+}
+
+}  // namespace idsk
+
+namespace {
 
 id_status copy_out(id_sketch* h, void* dst, const void* src, size_t bytes) {
   if (!dst || bytes == 0) return ID_OK;
@@ -438,17 +461,10 @@ id_status id_sketch_reset(id_sketch* h) {
 id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out) {
   if (!h) return ID_ERR_INVALID_ARG;
   if (h->poisoned) return ID_ERR_CUDA;
-  id_status s = launch_pending(h);
+  id_status s = factor_enqueue(h);
   if (s != ID_OK) return s;
   const int64_t n = h->n_seen;
-  if (n == 0) return ID_ERR_STATE;
-  const int k = h->k, l = h->l;
-  IDSK_CUDA(h, cudaMemcpy2DAsync(h->d_work, sizeof(double) * n, h->d_W,
-                                 sizeof(double) * h->n_max, sizeof(double) * n, l,
-                                 cudaMemcpyDeviceToDevice, h->st));
-  IDSK_CUDA(h, launch_cpqr_small(h->d_work, l, (int)n, (int)n, k, ID_RANK_TOL_FACTOR, h->d_R,
-                                 h->d_J, h->d_colpos, h->d_kout, h->st));
-  IDSK_CUDA(h, launch_solve_p(h->d_R, h->d_J, h->d_colpos, h->d_kout, k, (int)n, h->d_P, h->st));
+  const int k = h->k;
   if ((s = copy_out(h, J, h->d_J, sizeof(int32_t) * k)) != ID_OK) return s;
   if ((s = copy_out(h, P, h->d_P, sizeof(double) * k * n)) != ID_OK) return s;
   int32_t kk = 0, dst = 0;

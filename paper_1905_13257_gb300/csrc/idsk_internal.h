@@ -309,4 +309,10 @@ cudaError_t launch_single_pass_lift(const InterpGeom& g, int64_t m, int dtype, i
                                     cudaStream_t st);
 void gaussian_table_host(float* vals, uint16_t* bits);
 void count_launches(int64_t n);
+// Launch the sketch of every pending column window of the handle (capi.cu).
+id_status launch_pending(id_sketch* h);
+// Enqueue the randomized ID of the streamed columns (pivoted QR of W and the
+// solve for P) into h->d_J, h->d_P, h->d_kout, with no host synchronisation
+// (capi.cu).  ID_ERR_STATE when no column was streamed.
+id_status factor_enqueue(id_sketch* h);
 }  // namespace idsk

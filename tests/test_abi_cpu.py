@@ -87,3 +87,43 @@ def test_null_arguments_rejected(lib):
     assert lib.id_factor(None, None, None, None) == 1
     assert lib.id_gaussian_fill(3, 0, 0, 1, 1, None, None) == 1
     lib.id_sketch_destroy(None)
+
+
+def test_batch_problem_struct_layout(lib):
+    from paper_1905_13257_gb300 import _binding
+    assert C.sizeof(_binding.IdBatchProblem) == 56
+    assert _binding.IdBatchProblem.seed.offset == 48
+
+
+def _prob(**kw):
+    from paper_1905_13257_gb300 import _binding
+    p = _binding.IdBatchProblem()
+    p.d_A, p.lda, p.m, p.n, p.k, p.l, p.seed = 4096, 1000, 1000, 64, 4, 8, 1
+    for key, v in kw.items():
+        setattr(p, key, v)
+    return p
+
+
+@pytest.mark.parametrize("bad", [dict(d_A=None), dict(m=0), dict(lda=999), dict(n=0),
+                                 dict(n=513), dict(k=0), dict(k=9, l=8), dict(l=65),
+                                 dict(k=65, l=64, n=64),
+                                 dict(dtype=2), dict(prec=2), dict(prec=1, dtype=1),
+                                 dict(reserved=1)])
+def test_invalid_batch_rejected_before_any_gpu_call(lib, bad):
+    from paper_1905_13257_gb300 import _binding
+    arr = (_binding.IdBatchProblem * 2)(_prob(), _prob(**bad))
+    h = C.c_void_p(123)
+    assert lib.id_batch_create(arr, 2, None, C.byref(h)) == 1
+    assert h.value is None
+
+
+def test_batch_count_limits(lib):
+    from paper_1905_13257_gb300 import _binding
+    arr = (_binding.IdBatchProblem * 1)(_prob())
+    h = C.c_void_p()
+    assert lib.id_batch_create(arr, 0, None, C.byref(h)) == 1
+    assert lib.id_batch_create(arr, _binding.ID_BATCH_MAX_PROBLEMS + 1, None, C.byref(h)) == 1
+    assert lib.id_batch_create(None, 1, None, C.byref(h)) == 1
+    assert lib.id_batch_run(None, None, None, None) == 1
+    assert lib.id_batch_wait(None, None) == 1
+    lib.id_batch_destroy(None)

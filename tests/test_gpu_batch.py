@@ -1,0 +1,154 @@
+"""GPU parity of the batched form (id_batch_*): every problem of one
+graph-launched batch against the oracle's randomized ID (Algorithm 4,
+Sec. 2.4) on the same Psi and Omega, and against one handle per problem.
+
+Bars as for the single-handle randomized ID: k_out equal, P(:, J) = I exactly,
+J equal where the oracle's pivot margin is >= 1e-4, P within 1e-3 (FP32 data,
+FP32-accurate sketch) or 1e-10 (FP64) of the oracle's, relative to max(1,
+max|P|); against one handle on the same data J equal and P within 1e-9.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synthetic import channel_field, low_rank_matrix
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+# grid (nx = nz = 2 ny, 3 components), n, k, l, dtype, sketch precision
+CASES = [
+    ((8, 4, 8), 40, 6, 16, torch.float32, "exact"),      # m = 768
+    ((12, 6, 12), 97, 12, 22, torch.float32, "exact"),   # m = 2,592, ragged n
+    ((16, 8, 16), 200, 20, 30, torch.float32, "bf16"),   # m = 6,144, BF16 form
+    ((20, 10, 20), 512, 30, 40, torch.float32, "exact"),  # m = 12,000, n at the limit
+    ((16, 8, 16), 300, 16, 26, torch.float64, "exact"),  # FP64 data (SIMT sketch)
+    ((8, 4, 8), 64, 10, 64, torch.float64, "exact"),     # l at the limit
+    ((24, 12, 24), 130, 24, 34, torch.float32, "exact"),  # m = 20,736
+]
+
+
+def make_problems(seed0):
+    probs = []
+    for i, (grid, n, k, l, dtype, prec) in enumerate(CASES):
+        A = channel_field(grid, 3, n, seed=seed0 + i, gap_k=k, dtype=dtype, device=DEV)
+        probs.append(dict(A=A, k=k, l=l, seed=100 + i, prec=prec))
+    return probs
+
+
+def oracle_id(p):
+    A = p["A"]
+    An = (A.to(torch.bfloat16) if p.get("prec") == "bf16" else A).double().cpu().numpy()
+    m, n = An.shape
+    Wo, _ = oracle.sketch(An, oracle.psi(p["l"], m, p["seed"]), oracle.omega(n, p["l"], p["seed"]))
+    return oracle.column_id(Wo, p["k"])
+
+
+def check_against_oracle(p, J, P, kout):
+    Jo, Po, ko, margin = oracle_id(p)
+    k = p["k"]
+    assert kout == ko == k
+    Jg, Pg = J.cpu().numpy(), P.cpu().numpy()
+    assert np.array_equal(Pg[:, Jg], np.eye(k))
+    if margin < 1e-4:      # pivots within rounding of a tie: J is not unique
+        return
+    assert Jg.tolist() == Jo.tolist()
+    tol = 1e-10 if p["A"].dtype == torch.float64 else 1e-3
+    assert np.max(np.abs(Pg - Po)) <= tol * max(1.0, np.max(np.abs(Po)))
+
+
+def test_batch_matches_oracle_and_single_handles():
+    from paper_1905_13257_gb300 import IdBatch, IdSketch
+    probs = make_problems(seed0=20)
+    bt = IdBatch(probs)
+    bt.run()
+    res = bt.wait()
+    assert len(res) == len(probs)
+    for p, (J, P, kout) in zip(probs, res):
+        check_against_oracle(p, J, P, kout)
+        A = p["A"]
+        sk = IdSketch(m=A.shape[0], n_max=A.shape[1], k=p["k"], l=p["l"], seed=p["seed"],
+                      dtype=A.dtype, prec=p["prec"], want_Y=False)
+        sk.stream_columns(A)
+        J1, P1, k1 = sk.factor()
+        assert k1 == kout
+        assert J1.tolist() == J.tolist()
+        P1n = P1.cpu().numpy()
+        assert np.max(np.abs(P.cpu().numpy() - P1n)) <= 1e-9 * max(1.0, np.abs(P1n).max())
+        sk.close()
+    bt.close()
+
+
+def test_batch_replay_reads_new_data_and_counts_launches():
+    from paper_1905_13257_gb300 import IdBatch, load
+    lib = load()
+    probs = make_problems(seed0=40)
+    bt = IdBatch(probs)
+    bt.run()
+    bt.wait()
+    # the graph is captured: a replay launches the same kernels again
+    l0 = lib.id_kernel_launches()
+    bt.run()
+    bt.wait()
+    per_run = lib.id_kernel_launches() - l0
+    assert per_run >= 3 * len(probs)
+    # overwrite the data in place: the replay must see the new matrices
+    for i, p in enumerate(probs):
+        grid, n, k = CASES[i][0], CASES[i][1], CASES[i][2]
+        p["A"].copy_(channel_field(grid, 3, n, seed=70 + i, gap_k=k, dtype=p["A"].dtype,
+                                   device=DEV))
+    l1 = lib.id_kernel_launches()
+    bt.run()
+    res = bt.wait()
+    assert lib.id_kernel_launches() - l1 == per_run
+    for i in (0, 3, 4):
+        check_against_oracle(probs[i], *res[i])
+    bt.close()
+
+
+def test_batch_rank_deficient_problem():
+    from paper_1905_13257_gb300 import IdBatch
+    A1 = low_rank_matrix(3000, 60, 5, seed=3, dtype=torch.float64, device=DEV)
+    A2 = channel_field((8, 4, 8), 3, 50, seed=4, gap_k=8, dtype=torch.float32, device=DEV)
+    probs = [dict(A=A1, k=12, l=20, seed=5), dict(A=A2, k=8, l=18, seed=6)]
+    bt = IdBatch(probs)
+    bt.run()
+    (J1, P1, k1), (J2, P2, k2) = bt.wait()
+    Jo, Po, ko, _ = oracle.column_id(
+        oracle.sketch(A1.cpu().numpy(), oracle.psi(20, 3000, 5), oracle.omega(60, 20, 5))[0], 12)
+    assert k1 == ko == 5
+    assert J1.cpu().tolist()[5:] == [-1] * 7
+    assert k2 == 8
+    check_against_oracle(probs[1], J2, P2, k2)
+    bt.close()
+
+
+def test_batch_output_pointers_and_errors():
+    from paper_1905_13257_gb300 import IdBatch, IdError, load
+    from paper_1905_13257_gb300 import _binding as B
+    lib = load()
+    probs = make_problems(seed0=60)[:3]
+    bt = IdBatch(probs)
+    with pytest.raises(IdError) as e:          # no run yet
+        bt.wait()
+    assert e.value.status == B.ID_ERR_STATE
+    bt.run()
+    first = [(J.clone(), P.clone(), k) for J, P, k in bt.wait()]
+    # host output pointers are rejected
+    Jh = torch.empty_like(bt.J, device="cpu")
+    Ph = torch.empty_like(bt.P, device="cpu")
+    kh = torch.empty_like(bt.kout, device="cpu")
+    st = lib.id_batch_run(bt.h, C.c_void_p(Jh.data_ptr()), C.c_void_p(Ph.data_ptr()),
+                          C.c_void_p(kh.data_ptr()))
+    assert st == B.ID_ERR_INVALID_ARG
+    # other device outputs: the batch captures again and writes there
+    bt.J, bt.P, bt.kout = torch.zeros_like(bt.J), torch.zeros_like(bt.P), torch.zeros_like(bt.kout)
+    bt.run()
+    for (J, P, k), (J0, P0, k0) in zip(bt.wait(), first):
+        assert k == k0 and torch.equal(J, J0)
+        assert torch.allclose(P, P0, rtol=0, atol=1e-12)
+    bt.close()
