@@ -106,7 +106,7 @@ struct SketchArgs {
   void* Ac;             // mc x n_max, column-major, dtype
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
-  double* wpart;        // tensor-core kernel: per-CTA FP64 W^T slabs [nsm][64][512]
+  float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][64]
 };
 
 // ------------------------------------------------ single-pass ID (Alg. 6)
@@ -228,7 +228,7 @@ struct id_sketch {
   int sketch_kernel = 0;         // 0 auto, 1 tensor cores, 2 SIMT (IDSKETCH_SKETCH)
   int drain_blocks = 8;          // row blocks between FP64 flushes of W^T (tensor cores)
   int* d_status = nullptr;       // nonzero: a bounded device wait gave up
-  double* d_wpart = nullptr;     // per-CTA W^T slabs of the tensor-core sketch
+  float* d_wpart = nullptr;      // per-CTA W^T slabs of the tensor-core sketch
 
   // factor workspace
   double* d_work = nullptr;   // l x n_max copy of W

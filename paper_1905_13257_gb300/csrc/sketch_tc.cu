@@ -11,8 +11,10 @@
 // bfloat16 (quantile table), so every tensor-core product is exact and the
 // sketches carry only the split error (about 2.4e-6 relative in Frobenius
 // norm for NP = 2) and the FP32 accumulation.  NP = 1 is the bfloat16
-// precision form.  W^T partials are flushed to FP64 in global memory every
-// few row blocks.
+// precision form.  The tensor cores' FP32 accumulator error grows with the
+// length of the sum, so W^T partials leave TMEM every few row blocks; they
+// are added (round to nearest) into a per-CTA FP32 slab, about 30 partials
+// per entry, and the slabs are summed in FP64.
 //
 // Shared-memory layout.  A piece tile is stored in 128-byte-swizzled 1 KB
 // atoms of 8 columns x 64 rows (rows contiguous).  Read as K-major it is the
@@ -27,7 +29,11 @@
 //                split into pieces, store them to the swizzled piece buffer
 //                (double-buffered), gather coarse rows
 //   warps 8-11   epilogue: draw Psi for upcoming row blocks (counter
-//                generator), drain Y to global memory, flush W^T to FP64
+//                generator), drain Y to global memory, flush W^T partials
+//                into a per-CTA FP32 slab in L2 (one 128-column tile at a
+//                time, staggered over the row blocks: a tile's accumulator
+//                is handed back to the MMAs as soon as it is in registers,
+//                before its reductions)
 //   warp 12      TMEM allocation and the single-thread tcgen05.mma issue
 // 13 warps keep at most 4 warps per SM sub-partition, so a thread may hold
 // up to 128 registers.
@@ -84,8 +90,8 @@ __device__ long long g_tc_trace[4][8192];
 
 // barrier slots
 enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE1,
-       B_YF0, B_YF1, B_YE0, B_YE1, B_WF, B_WE, B_DONE, B_RF0, B_RE0 = B_RF0 + NST,
-       NBAR = B_RE0 + NST };
+       B_YF0, B_YF1, B_YE0, B_YE1, B_WF0, B_WE0 = B_WF0 + kTcMaxTiles,
+       B_DONE = B_WE0 + kTcMaxTiles, B_RF0, B_RE0 = B_RF0 + NST, NBAR = B_RE0 + NST };
 
 struct Smem {
   uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES] (TMA form: [2 slots][PIECE_BYTES])
@@ -98,12 +104,16 @@ struct Smem {
   uint32_t abort_flag;
 };
 
-__device__ __forceinline__ void st_f64_hint(double* p, double v, uint64_t policy) {
-  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
+__device__ __forceinline__ void st_v4_f32_hint(float* p, float a, float b, float c, float d,
+                                               uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d), "l"(policy)
                : "memory");
 }
-__device__ __forceinline__ void red_add_f64(double* p, double v, uint64_t policy) {
-  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(policy)
+__device__ __forceinline__ void red_add_v4_f32(float* p, float a, float b, float c, float d,
+                                               uint64_t policy) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+               "f"(a), "f"(b), "f"(c), "f"(d), "l"(policy)
                : "memory");
 }
 
@@ -192,8 +202,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     mbar_init(bar(B_YF1), 1);
     mbar_init(bar(B_YE0), NEPI);
     mbar_init(bar(B_YE1), NEPI);
-    mbar_init(bar(B_WF), 1);
-    mbar_init(bar(B_WE), NEPI);
+    for (int ct = 0; ct < kTcMaxTiles; ++ct) {
+      mbar_init(bar(B_WF0 + ct), 1);
+      mbar_init(bar(B_WE0 + ct), NEPI);
+    }
     mbar_init(bar(B_DONE), 1);
     if (TMA) {
       for (int st = 0; st < NST; ++st) {
@@ -227,7 +239,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
 
-  auto drain_due = [&](int i) { return ((i + 1) % drain_blocks) == 0 || i == nloc - 1; };
+  // W^T tile ct is flushed after row block i when drain_due(i, ct): every
+  // drain_blocks row blocks, the tiles offset from one another so that the
+  // flushes spread over the row blocks, and all tiles after the last one
+  auto drain_due = [&](int i, int ct) {
+    return ((i + 1 + (ct * drain_blocks) / kTcMaxTiles) % drain_blocks) == 0 || i == nloc - 1;
+  };
 
   if (warp < NCONV) {
     if constexpr (TMA) {
@@ -438,9 +455,52 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       if (lane == 0) mbar_arrive(bar(B_PSIF0 + pb));
     };
     for (int i = 0; i < 2 && i < nloc; ++i) gen_psi(i, i);
-    int wd = 0;
+    uint32_t wpar = 0, wseen = 0;   // per W^T tile: flush-count parity, flushed before
     for (int i = 0; i < nloc; ++i) {
       const int pb = i & 1;
+      // flushes due after this row block first: each W^T tile's barrier is
+      // committed right after that tile's MMAs, and the next row block's
+      // MMAs wait for the tile to be read out
+      bool wok = true;
+      for (int ct = 0; ct < nct; ++ct) {
+        if (!drain_due(i, ct)) continue;
+        if (!mbar_wait(bar(B_WF0 + ct), (wpar >> ct) & 1u, S.abort_flag, 256)) {
+          wok = false;
+          break;
+        }
+        tc_fence_after();
+        // the tile's 128 x 64 partials into registers; the accumulator then
+        // goes back to the MMAs while the partials are added to this CTA's
+        // private FP32 slab wpart[cta][c][s] (the first flush of a tile
+        // stores, later ones add in L2, four entries per reduction; each slab
+        // entry is written by one thread only, in program order, so the sum
+        // has a fixed order)
+        float v[2][32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP), v[0]);
+        tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP + 32), v[1]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_WE0 + ct));
+        const uint64_t keep = policy_evict_last();
+        float* dst =
+            a.wpart + ((int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) + ct * TCOLS + rl) * LP;
+        const bool first = !((wseen >> ct) & 1u);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            if (first)
+              st_v4_f32_hint(dst + h * 32 + j, v[h][j], v[h][j + 1], v[h][j + 2], v[h][j + 3],
+                             keep);
+            else
+              red_add_v4_f32(dst + h * 32 + j, v[h][j], v[h][j + 1], v[h][j + 2], v[h][j + 3],
+                             keep);
+          }
+        }
+        wpar ^= 1u << ct;
+        wseen |= 1u << ct;
+      }
+      if (!wok) break;
       if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
       tc_fence_after();
       {
@@ -469,39 +529,6 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_YE0 + pb));
-      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i);
-      if (drain_due(i)) {
-        if (!mbar_wait(bar(B_WF), wd & 1, S.abort_flag, 256)) break;
-        tc_fence_after();
-        // W^T partials -> this CTA's private FP64 slab wpart[cta][s][c]: the
-        // first flush of the launch stores, later ones add in L2.  Each slab
-        // entry is written by one thread only, in program order, so the sum is
-        // taken in a fixed order.
-        double* slab = a.wpart + (int64_t)blockIdx.x * LP * (kTcMaxTiles * TCOLS);
-        const uint64_t keep = policy_evict_last();
-        for (int ct = 0; ct < nct; ++ct) {
-          const int c = ct * TCOLS + rl;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP + h * 32), v);
-            double* dst = slab + (int64_t)(h * 32) * (kTcMaxTiles * TCOLS) + c;
-            if (wd == 0) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                st_f64_hint(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j], keep);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                red_add_f64(dst + (int64_t)j * (kTcMaxTiles * TCOLS), (double)v[j], keep);
-            }
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_WE));
-        ++wd;
-      }
       if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 1);
       if (i + 2 < nloc) {
         if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
@@ -511,8 +538,9 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     }
   } else if (warp == MMA_WARP && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    uint32_t accw = 0;   // bit ct: W^T accumulator of tile ct holds data
-    int wd = 0;
+    uint32_t accw = 0;    // bit ct: W^T accumulator of tile ct holds data
+    uint32_t wpend = 0;   // bit ct: tile ct handed to the epilogue, not yet read out
+    uint32_t wpar = 0;    // bit ct: parity of the flushes of tile ct handed out
     int t = 0;
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
@@ -529,6 +557,13 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           break;
         }
         TC_TRACE(1, t);
+        if ((wpend >> ct) & 1u) {   // the epilogue must have read the last flush
+          if (!mbar_wait(bar(B_WE0 + ct), ((wpar >> ct) & 1u) ^ 1u, S.abort_flag)) {
+            ok = false;
+            break;
+          }
+          wpend &= ~(1u << ct);
+        }
         tc_fence_after();
         const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
         const uint32_t wtm = tmem + (uint32_t)(ct * LP);
@@ -564,17 +599,16 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         if (!ok) break;
         accw |= 1u << ct;
         if (!TMA) mma_commit(bar(B_FREE0 + b));
+        if (drain_due(i, ct)) {   // hand tile ct's partials to the epilogue
+          mma_commit(bar(B_WF0 + ct));
+          wpar ^= 1u << ct;
+          wpend |= 1u << ct;
+          accw &= ~(1u << ct);
+        }
       }
       if (!ok) break;
       mma_commit(bar(B_YF0 + pb));
       mma_commit(bar(B_PSIE0 + pb));
-      if (drain_due(i)) {
-        mma_commit(bar(B_WF));
-        if (!mbar_wait(bar(B_WE), wd & 1, S.abort_flag)) break;
-        tc_fence_after();
-        ++wd;
-        accw = 0;
-      }
     }
     // every issued MMA has completed before the TMEM is released
     mma_commit(bar(B_DONE));
@@ -617,18 +651,19 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   if (tid == 0 && ld_volatile_shared(S.abort_flag)) atomicOr(status, 1);
 }
 
-// W(:, window) = sum over CTAs of their slabs, in CTA order (deterministic).
-// A CTA whose row range is empty never wrote its slab and is skipped.
-__global__ void wpart_reduce_kernel(const double* __restrict__ wpart, int nslab, int l, int ncols,
+// W(:, window) = sum over CTAs of their slabs, in FP64 and CTA order
+// (deterministic).  A CTA whose row range is empty never wrote its slab and
+// is skipped.
+__global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, int l, int ncols,
                                     int64_t nrb, double* __restrict__ W, int64_t ldw,
                                     int64_t col_base) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * ncols) return;
-  const int s = e / ncols, c = e - s * ncols;
+  const int c = e / l, s = e - c * l;
   double acc = 0.0;
   for (int b = 0; b < nslab; ++b) {
     if (nrb * (b + 1) / nslab == nrb * b / nslab) continue;
-    acc += wpart[((int64_t)b * LP + s) * (kTcMaxTiles * TCOLS) + c];
+    acc += (double)wpart[((int64_t)b * (kTcMaxTiles * TCOLS) + c) * LP + s];
   }
   W[(int64_t)s * ldw + col_base + c] = acc;
 }
