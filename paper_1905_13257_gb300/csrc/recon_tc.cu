@@ -105,7 +105,11 @@ __device__ __forceinline__ void split3(float x, uint16_t& p0, uint16_t& p1, uint
 // TMA: A(R, C) reaches the epilogue through an NST-stage ring of TMA boxes
 // (producer warp 13) and the skeleton pieces are single-buffered to make room;
 // otherwise the epilogue loads A itself and the pieces are double-buffered.
-template <bool TMA>
+// INTERP: the skeleton rows are interpolated from the coarse skeleton
+// (single-pass ID) instead of gathered from A; a separate instantiation, so
+// that the plain error pass carries none of that code (the kernel's roles
+// share the instruction cache).
+template <bool TMA, bool INTERP>
 __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     recon_tc_kernel(const float* __restrict__ A, int64_t lda, int64_t m, int n,
                     const int* __restrict__ J, const double* __restrict__ P, int k,
@@ -199,6 +203,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       const int b = i & 1;
       const int64_t r = (rb_begin + i) * TR + q * 32 + lane;
       const bool rok = r < m;
+#pragma unroll 1
       for (int c4 = 0; c4 < 4; ++c4) {
         const int cb = c0 + ch * 128 + c4 * 32;
         const bool full = rok && (cb + 31 < n);
@@ -279,15 +284,45 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     // ---------------------------------------------------------------- gather
     const int rl = tid - NEPI * 32;          // row of the block owned by this thread
     uint8_t* sm_gen = smem_raw + (s_s - smem_u32(smem_raw));
-    for (int i = 0; i < nloc; ++i) {
+    // 8 skeleton values of this row, entries t0..t0+7: split into the three
+    // pieces and stored as one 16-byte chunk of each piece
+    auto store8 = [&](uint8_t* sbp, int t0, const float* x8) {
+      uint32_t w[3][4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        uint16_t a0, a1, a2, b0, b1, b2;
+        split3(x8[u], a0, a1, a2);
+        split3(x8[u + 1], b0, b1, b2);
+        w[0][u >> 1] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+        w[1][u >> 1] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+        w[2][u >> 1] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+      }
+      const uint32_t off = swz((uint32_t)rl, (uint32_t)t0, 1024u);   // 16 bytes
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+        *reinterpret_cast<uint4*>(sbp + p * S_PIECE + off) =
+            make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    };
+    bool gok = true;
+    for (int i = 0; i < nloc && gok; ++i) {
       const int b = i % NSB, use = i / NSB;
       const int64_t r = (rb_begin + i) * TR + rl;
       const bool rok = r < m;
-      float x[KP];
-      if (geo.Sc == nullptr) {
+      uint8_t* sbp = sm_gen + (size_t)b * 3u * S_PIECE;
+      if constexpr (!INTERP) {
+        // all k loads of the row in flight at once (the gather warps are on
+        // the error pass's critical path), then split and stored
+        float x[KP];
 #pragma unroll
         for (int t = 0; t < KP; ++t) x[t] = (t < k && rok) ? A[r + (int64_t)Js[t] * lda] : 0.f;
+        if (use >= 1 && !mbar_wait(bar(B_SE0 + b), (use - 1) & 1, abort_flag, 64)) {
+          gok = false;
+          break;
+        }
+#pragma unroll
+        for (int t0 = 0; t0 < KP; t0 += 8) store8(sbp, t0, x + t0);
       } else {   // single-pass ID: the skeleton row interpolated from the coarse one
+        float x[KP];
 #pragma unroll
         for (int t = 0; t < KP; ++t) x[t] = 0.f;
         if (rok) {
@@ -310,26 +345,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             }
           }
         }
-      }
-      if (use >= 1 && !mbar_wait(bar(B_SE0 + b), (use - 1) & 1, abort_flag, 64)) break;
-      uint8_t* sbp = sm_gen + (size_t)b * 3u * S_PIECE;
-#pragma unroll
-      for (int t0 = 0; t0 < KP; t0 += 8) {
-        uint32_t w[3][4];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          uint16_t a0, a1, a2, b0, b1, b2;
-          split3(x[t0 + u], a0, a1, a2);
-          split3(x[t0 + u + 1], b0, b1, b2);
-          w[0][u >> 1] = (uint32_t)a0 | ((uint32_t)b0 << 16);
-          w[1][u >> 1] = (uint32_t)a1 | ((uint32_t)b1 << 16);
-          w[2][u >> 1] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+        if (use >= 1 && !mbar_wait(bar(B_SE0 + b), (use - 1) & 1, abort_flag, 64)) {
+          gok = false;
+          break;
         }
-        const uint32_t off = swz((uint32_t)rl, (uint32_t)t0, 1024u);   // 16 bytes
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
-          *reinterpret_cast<uint4*>(sbp + p * S_PIECE + off) =
-              make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        for (int t0 = 0; t0 < KP; t0 += 8) store8(sbp, t0, x + t0);
       }
       fence_proxy_async();
       __syncwarp();
@@ -425,7 +446,9 @@ cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, c
   const bool tma = !(env && env[0] == '0') && make_tmap_f32_2d(A, m, n, lda, TR, 32, &tm);
   const size_t sm = 1024 + 3u * P_PIECE + (tma ? 3u * S_PIECE + NST * RAW_BYTES : 6u * S_PIECE) +
                     NBAR * 8 + 16;
-  auto kern = tma ? recon_tc_kernel<true> : recon_tc_kernel<false>;
+  const bool ip = interp != nullptr && interp->Sc != nullptr;
+  auto kern = tma ? (ip ? recon_tc_kernel<true, true> : recon_tc_kernel<true, false>)
+                  : (ip ? recon_tc_kernel<false, true> : recon_tc_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (timer && (e = timer->mark(st)) != cudaSuccess) return e;

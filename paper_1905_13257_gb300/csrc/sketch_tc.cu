@@ -129,6 +129,23 @@ __device__ __forceinline__ bool conv_bar_or(bool v) {
   return r != 0;
 }
 
+// Coarse rows of one raw column (128 rows in shared memory): this thread's
+// rows rq + 32 g + q (g, q < 4) whose coarse index is set go to A_c.  Only
+// row blocks that hold coarse rows come here; the loop stays rolled and out
+// of line because the converters' unrolled loop must fit the instruction
+// cache (inlined, the gather made the kernel 17% larger and 42% slower).
+__device__ __noinline__ void gather_column(const float* col, const int64_t* rcs, int rq,
+                                           float* Ac) {
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g)
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int rr = 32 * g + rq + q;
+      const int64_t rcv = rcs[rr];
+      if (rcv >= 0) Ac[rcv] = col[rr];
+    }
+}
+
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
   const int64_t i = r % g.nx;
   const int64_t rest = r / g.nx;
@@ -310,16 +327,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
               lo_keep[(j * 4 + g) * 2] = pack_bf16x2(x.x - f01.x, x.y - f01.y);
               lo_keep[(j * 4 + g) * 2 + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
             }
-            if (gather && wc < w.ncols) {
-              float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc);
-              const float xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-              for (int q4 = 0; q4 < 4; ++q4) {
-                const int64_t rcv = rcs[rr + q4];
-                if (rcv >= 0) Ac[rcv] = xs[q4];
-              }
-            }
           }
+          if (gather && wc < w.ncols)
+            gather_column(raw + cl * TR, rcs, rq,
+                          reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc));
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_RE0 + st));
         }

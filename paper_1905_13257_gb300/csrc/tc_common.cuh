@@ -46,9 +46,18 @@ __device__ __forceinline__ void st_volatile_shared(uint32_t a, int v) {
 // timeout or when another role already aborted.  Between polls the thread
 // sleeps (sleep_ns), so that waiting roles leave the issue slots to the
 // converter warps that share their schedulers.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag,
-                          uint32_t sleep_ns = 64) {
+// The first poll is inline; the polling loop is out of line, so that a
+// kernel with many wait sites stays small (warp-specialised kernels run
+// several roles' code at once and are bound by the instruction cache).
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
+                                                   uint32_t abort_flag, uint32_t sleep_ns);
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag,
+                                          uint32_t sleep_ns = 64) {
   if (mbar_try(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, sleep_ns);
+}
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
+                                                   uint32_t abort_flag, uint32_t sleep_ns) {
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     __nanosleep(sleep_ns);
