@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           ok = false;
           break;
         }
+        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t);
         const uint32_t hi_buf = S.pieces + (uint32_t)s0 * PIECE_BYTES;
         uint32_t lo_keep[NP > 1 ? 32 : 1];   // second piece, packed, until its slot frees
 #pragma unroll
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           const int u = 4 * t + j, st = u % NST;
           if (ok && !mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) ok = false;
           if (!ok) continue;
+          if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 1 + j);
           const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
           const int cc = 32 * j + cl;              // column inside the tile
           const int wc = ct * TCOLS + cc;          // column inside the window
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_FULL0 + s0));
+        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 5);
         if (NP > 1) {
           const int u1 = u0 + 1;   // slot 1
           if ((u1 >> 1) >= 1 &&
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             ok = false;
             break;
           }
+          if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 6);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_FULL1));
         }
-        if (warp == 0 && lane == 0) TC_TRACE(0, t);
+        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 7);
       }
     }
     } else {
@@ -512,8 +516,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         wseen |= 1u << ct;
       }
       if (!wok) break;
+      if (q == 0 && lane == 0) TC_TRACE(2, 4 * i);
       if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
       tc_fence_after();
+      if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 1);
       {
         const int64_t r = (rb_begin + i) * TR + rl;
         float* Y = reinterpret_cast<float*>(a.Y);
@@ -540,12 +546,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_YE0 + pb));
-      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 1);
+      if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 2);
       if (i + 2 < nloc) {
         if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
         gen_psi(i + 2, pb);
       }
-      if (q == 0 && lane == 0) TC_TRACE(2, 3 * i + 2);
+      if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 3);
     }
   } else if (warp == MMA_WARP && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -567,7 +573,6 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           ok = false;
           break;
         }
-        TC_TRACE(1, t);
         if ((wpend >> ct) & 1u) {   // the epilogue must have read the last flush
           if (!mbar_wait(bar(B_WE0 + ct), ((wpar >> ct) & 1u) ^ 1u, S.abort_flag)) {
             ok = false;
@@ -588,6 +593,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
               ok = false;
               break;
             }
+            TC_TRACE(1, 2 * u);
             tc_fence_after();
             pa = S.pieces + (uint32_t)(u & 1) * PIECE_BYTES;
           }
@@ -606,6 +612,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
                      sdesc(om + ko, 0u, 2048u), IDESC_Y, acc);
           }
           if (TMA) mma_commit(bar(B_FREE0 + (u & 1)));
+          TC_TRACE(1, 2 * u + 1);
         }
         if (!ok) break;
         accw |= 1u << ct;
@@ -645,6 +652,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           ok = false;
           break;
         }
+        TC_TRACE(3, u);
         mbar_expect_tx(bar(B_RF0 + st), RAW_BYTES);
         tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES, tm, row, ct * TCOLS + 32 * j,
                     bar(B_RF0 + st), stream_once);
@@ -711,6 +719,18 @@ cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int d
 }
 
 }  // namespace
+
+#ifdef IDSK_TC_TRACE
+// Profiling harness only: the clock64 timeline of CTA 0 ([4][8192]): role 0
+// converter warp 0 (per tile t: 8t start, 8t+1+j box j in, 8t+5 first piece
+// out, 8t+6 second slot free, 8t+7 second piece out), role 1 MMA (2u piece
+// unit u ready, 2u+1 issued), role 2 epilogue (per row block i: 4i flushes
+// done, 4i+1 Y ready, 4i+2 Y drained, 4i+3 Psi drawn), role 3 producer (box u
+// issued).
+extern "C" int idsk_tc_trace_read(long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, g_tc_trace, sizeof(g_tc_trace));
+}
+#endif
 
 cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
                              int drain_blocks, int* status, cudaStream_t st, KernelTimer* timer) {
