@@ -334,6 +334,28 @@ def test_tensor_core_sketch_feeds(monkeypatch, tma):
     sk.close()
 
 
+@pytest.mark.parametrize("drain", ["1", "3", "5", "8", "64"])
+def test_sketch_flush_schedules(monkeypatch, drain):
+    """W^T partials leave TMEM one 128-column tile at a time, every `drain` row
+    blocks with the four tiles offset by drain / 4 row blocks, and the last
+    row block flushes them all.  Every schedule (shorter than the four tiles,
+    uneven offsets, longer than a CTA's row range) gives the oracle's
+    sketches within the FP32 bar."""
+    monkeypatch.setenv("IDSKETCH_DRAIN_BLOCKS", drain)
+    grid, nc, n, l = (32, 24, 32), 3, 400, 60        # 576 row blocks, 4 column tiles
+    A = channel_field(grid, nc, n, seed=12, dtype=torch.float32, device=DEV)
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=n, k=10, l=l, seed=13, dtype=torch.float32, want_Y=True,
+             window_cols=n)
+    stream(sk, A, [32] * (n // 32) + [n % 32])
+    W, Y, _ = sk.sketches()
+    Wo, Yo = oracle.sketch(A.cpu().double().numpy(), oracle.psi(l, m, 13),
+                           oracle.omega(n, l, 13))
+    assert rel(W.cpu().numpy(), Wo) <= 1e-5
+    assert rel(Y.cpu().double().numpy(), Yo) <= 1e-5
+    sk.close()
+
+
 # ------------------------------------------------------------ kernel timing
 
 def test_kernel_timing_counts_launches():
