@@ -250,13 +250,13 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
       float2 u = make_float2(0.f, 0.f);
       if (i >= s) {
         u = df_of((double)Ac[i + (int64_t)p * mc]);
-        for (int t0 = 0; t0 < s; t0 += 8) {   // 8 loads of V in flight, then the sums
-          float2 vv[8];
+        for (int t0 = 0; t0 < s; t0 += 16) {   // 16 loads of V in flight, then the sums
+          float2 vv[16];
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
+          for (int q = 0; q < 16; ++q)
             vv[q] = t0 + q < s ? V[(int64_t)(t0 + q) * mc + i] : make_float2(0.f, 0.f);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 16; ++q) {
             if (t0 + q < s) {
               const float2 pr = df_mul(vv[q], fp[t0 + q]);
               df_add(u.x, u.y, -pr.x, -pr.y);
@@ -274,25 +274,35 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
     const float2 u2 = df_mul(uu, uu);
     df_add(sig.x, sig.y, u2.x, u2.y);
     __syncthreads();
-    // V_s^T u: warp w takes t = w + 8q, each lane keeps partials over its rows
+    // V_s^T u: warp w takes t = w + 8q, each lane keeps partials over its rows.
+    // The loads of four quantities x 4 rows per lane are in flight together;
+    // every partial still adds its rows in the same order.
 #pragma unroll
-    for (int q = 0; q < kLMax / 8; ++q) {
-      const int t = warp + 8 * q;
-      if (t < s) {
-        const float2* vc = V + (int64_t)t * mc + c0;
-        for (int k0 = 0; k0 < nrow; k0 += 128) {   // 4 rows per lane in flight
-          float2 vv[4];
+    for (int qg = 0; qg < kLMax / 8; qg += 4) {
+      if (warp + 8 * qg >= s) continue;
+      for (int k0 = 0; k0 < nrow; k0 += 128) {
+        float2 vv[4][4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int t = warp + 8 * (qg + qq);
+          const float2* vc = V + (int64_t)t * mc + c0;
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int k = k0 + 32 * e + lane;
-            vv[e] = k < nrow ? vc[k] : make_float2(0.f, 0.f);
+            vv[qq][e] = (t < s && k < nrow) ? vc[k] : make_float2(0.f, 0.f);
           }
+        }
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = k0 + 32 * e + lane;
-            if (k < nrow) {
-              const float2 pr = df_mul(vv[e], ud[k]);
-              df_add(hacc[q].x, hacc[q].y, pr.x, pr.y);
+        for (int qq = 0; qq < 4; ++qq) {
+          const int q = qg + qq;
+          if (warp + 8 * q < s) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = k0 + 32 * e + lane;
+              if (k < nrow) {
+                const float2 pr = df_mul(vv[qq][e], ud[k]);
+                df_add(hacc[q].x, hacc[q].y, pr.x, pr.y);
+              }
             }
           }
         }
@@ -348,13 +358,22 @@ __global__ void __launch_bounds__(ST_THREADS) step_kernel(
   float ah[NQ], al[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) ah[q] = al[q] = 0.f;
-  for (int b = lane; b < G; b += 32) {   // all loads of an iteration in flight
+  for (int b = lane; b < G; b += 64) {   // two CTA strides of loads in flight
+    float2 x0[NQ], x1[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int qn = warp + 8 * q;
+      const bool use = qn < s || qn == kLMax;
+      const float2* hp2 = reinterpret_cast<const float2*>(hpart);
+      x0[q] = use ? hp2[(int64_t)b * HP + qn] : make_float2(0.f, 0.f);
+      x1[q] = (use && b + 32 < G) ? hp2[(int64_t)(b + 32) * HP + qn] : make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int qn = warp + 8 * q;
       if (qn < s || qn == kLMax) {
-        const float2 x = reinterpret_cast<const float2*>(hpart)[(int64_t)b * HP + qn];
-        df_add(ah[q], al[q], x.x, x.y);
+        df_add(ah[q], al[q], x0[q].x, x0[q].y);
+        if (b + 32 < G) df_add(ah[q], al[q], x1[q].x, x1[q].y);
       }
     }
   }
