@@ -57,6 +57,24 @@ def workload(grid=GRID, n=NSNAP):
 
 # ------------------------------------------------------------------ helpers
 
+def max_over_ranks(ms, device, world):
+    """The job's step time: the slowest rank's (an all-reduce MAX over the
+    process group; the value itself on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, bytes_per_rank_step, ms):
+    """Whole-job GB/s: the bytes every rank processed in one step over the
+    job's step time (weak scaling: one independent matrix per rank)."""
+    return world * bytes_per_rank_step / (ms / 1e3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -289,13 +307,10 @@ def run_ours(args):
     clk = clocks.stop()
     kt = {w: sk.read_timing(w) for w in ("sketch", "recon")}
     sk.timing(False)
-    ms = t_start.elapsed_time(t_end) / args.steps
+    ms = max_over_ranks(t_start.elapsed_time(t_end) / args.steps, dev, world)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * 4.0 * m * n / (ms / 1e3) / 1e9
+    value = job_throughput(world, 4.0 * m * n, ms)
 
     # roofline of the dominant kernel: the fused sketch (FP32 data takes the
     # tensor-core kernel, 512 columns per launch).  Algorithmic bytes of one
