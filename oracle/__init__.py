@@ -14,6 +14,11 @@ Modules
   single_pass    the single-pass ID of Algorithm 6 (Sec. 2.6): the
                  coarse-to-fine interpolation operator M on the mesh, the
                  interpolated skeleton, its error and the Theorem 2.2 bound
+  learned        the learned skeleton proposal (no counterpart in the paper):
+                 column features on a coarse sub-grid, a 2-layer GELU MLP
+                 with its loss, gradients and SGD step, the top-2k proposal,
+                 the pivoted QR restricted to it and the fallback rule
+                 (import as ``oracle.learned``)
 
 Parity status of each function is pinned by ``tests/test_oracle_*.py``; none
 is unpinned.
