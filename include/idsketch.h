@@ -277,6 +277,46 @@ id_status id_batch_wait(id_batch* b, int32_t* kout_host);
 /* Synchronise the batch's stream and release everything it holds. */
 void id_batch_destroy(id_batch* b);
 
+/* ---------------------------------------------------------------------
+ * Learned skeleton proposal: the network's kernels.  No counterpart in the
+ * paper (its conclusion motivates the ID as the selection of the most
+ * important snapshots, Sec. 4).  The network scores snapshot columns from
+ * coarse-grid features,
+ *   s = w2 . gelu(x W1 + b1) + b2,  gelu(z) = z Phi(z)  (exact GELU),
+ * and is trained on the skeletons the plain randomized ID picks, with the mean
+ * binary cross entropy of sigmoid(s) (positives weighted by pos_weight).
+ * All buffers are device FP32, row-major, caller-owned; the calls enqueue on
+ * cuda_stream (NULL = legacy default stream) and do not synchronise.  Every
+ * sum runs in a fixed order.  Errors: ID_ERR_INVALID_ARG (NULL pointer, a
+ * size below 1 or too large), ID_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+
+/* X (n x F): X[j * F + f] = scale * A(rows[f], j) for the n columns of A
+ * (device, column-major m x n, lda >= m, dtype); rows: F device int64 row
+ * indices (a row outside [0, m) gives a NaN feature, never an out-of-bounds
+ * read). */
+id_status id_mlp_features(const void* d_A, int64_t lda, int64_t m, int64_t n, int32_t dtype,
+                          const int64_t* d_rows, int64_t F, float scale, float* d_X,
+                          void* cuda_stream);
+
+/* Forward pass on n feature rows X (n x F): Z = X W1 + b1 (n x H), G =
+ * gelu(Z), s = G w2 + b2 (n).  W1: F x H; b1, w2: H; b2: 1 value. */
+id_status id_mlp_forward(const float* d_X, int64_t n, int64_t F, int32_t H, const float* d_W1,
+                         const float* d_b1, const float* d_w2, const float* d_b2, float* d_Z,
+                         float* d_G, float* d_s, void* cuda_stream);
+
+/* Gradients of the loss for targets y (n values in {0, 1}) from a forward
+ * pass's Z, G and s: gW1 (F x H), gb1 (H), gw2 (H), gb2 (1).  Scratch: ds (n),
+ * dZ (n x H). */
+id_status id_mlp_backward(const float* d_X, int64_t n, int64_t F, int32_t H, const float* d_Z,
+                          const float* d_G, const float* d_w2, const float* d_s,
+                          const float* d_y, float pos_weight, float* d_gW1, float* d_gb1,
+                          float* d_gw2, float* d_gb2, float* d_ds, float* d_dZ,
+                          void* cuda_stream);
+
+/* Gradient step p -= lr g over count values. */
+id_status id_mlp_sgd(float* d_p, const float* d_g, int64_t count, float lr, void* cuda_stream);
+
 /* Borrow the device buffers of the sketch (valid until reset/destroy):
  *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])
  *   Y  m x l, dtype, column-major (entry (i, s) at Y[i + s*m]); NULL unless want_Y

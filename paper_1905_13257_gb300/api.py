@@ -269,6 +269,74 @@ class IdBatch:
             pass
 
 
+def mlp_features(A, rows, scale=1.0, stream=None):
+    """X (n x F, FP32): row j holds scale * A(rows, j) (id_mlp_features).
+    A: m x n column-major CUDA tensor (FP32 or FP64); rows: int64 indices."""
+    lib = B.load()
+    sh, stream = _stream_handle(stream)
+    m = A.shape[0]
+    ld = _colmajor(A, m)
+    rows = torch.as_tensor(rows, dtype=torch.int64, device=A.device).contiguous()
+    X = torch.empty((A.shape[1], rows.numel()), dtype=torch.float32, device=A.device)
+    dt = B.ID_F64 if A.dtype == torch.float64 else B.ID_F32
+    B.check(lib.id_mlp_features(C.c_void_p(A.data_ptr()), ld, m, A.shape[1], dt,
+                                C.c_void_p(rows.data_ptr()), rows.numel(), C.c_float(scale),
+                                C.c_void_p(X.data_ptr()), sh), "id_mlp_features")
+    return X
+
+
+class Mlp:
+    """The learned proposal's network on the GPU (id_mlp_*): s = w2 .
+    gelu(x W1 + b1) + b2, parameters as FP32 CUDA tensors (W1: F x H)."""
+
+    def __init__(self, params, device="cuda", stream=None):
+        self.lib = B.load()
+        self._sh, self.stream = _stream_handle(stream)
+        f32 = dict(dtype=torch.float32, device=device)
+        self.W1 = torch.as_tensor(params["W1"], **f32).contiguous()
+        self.b1 = torch.as_tensor(params["b1"], **f32).contiguous()
+        self.w2 = torch.as_tensor(params["w2"], **f32).contiguous()
+        self.b2 = torch.as_tensor(params["b2"], **f32).reshape(1).contiguous()
+        self.F, self.H = self.W1.shape
+
+    def forward(self, X):
+        """Scores s (n); keeps Z and G for backward."""
+        X = X.to(torch.float32).contiguous()
+        n = X.shape[0]
+        self.Z = torch.empty((n, self.H), dtype=torch.float32, device=X.device)
+        self.G = torch.empty_like(self.Z)
+        self.s = torch.empty(n, dtype=torch.float32, device=X.device)
+        p = lambda t: C.c_void_p(t.data_ptr())   # noqa: E731
+        B.check(self.lib.id_mlp_forward(p(X), n, self.F, self.H, p(self.W1), p(self.b1),
+                                        p(self.w2), p(self.b2), p(self.Z), p(self.G), p(self.s),
+                                        self._sh), "id_mlp_forward")
+        return self.s
+
+    def backward(self, X, y, pos_weight=1.0):
+        """Gradients {W1, b1, w2, b2} of the loss at the last forward pass."""
+        X = X.to(torch.float32).contiguous()
+        y = torch.as_tensor(y, dtype=torch.float32, device=X.device).contiguous()
+        n = X.shape[0]
+        g = {"W1": torch.empty_like(self.W1), "b1": torch.empty_like(self.b1),
+             "w2": torch.empty_like(self.w2), "b2": torch.empty_like(self.b2)}
+        ds = torch.empty(n, dtype=torch.float32, device=X.device)
+        dZ = torch.empty_like(self.Z)
+        p = lambda t: C.c_void_p(t.data_ptr())   # noqa: E731
+        B.check(self.lib.id_mlp_backward(p(X), n, self.F, self.H, p(self.Z), p(self.G),
+                                         p(self.w2), p(self.s), p(y), C.c_float(pos_weight),
+                                         p(g["W1"]), p(g["b1"]), p(g["w2"]), p(g["b2"]), p(ds),
+                                         p(dZ), self._sh), "id_mlp_backward")
+        return g
+
+    def step(self, grads, lr):
+        """SGD: every parameter -= lr * its gradient."""
+        for name in ("W1", "b1", "w2", "b2"):
+            t = getattr(self, name)
+            B.check(self.lib.id_mlp_sgd(C.c_void_p(t.data_ptr()),
+                                        C.c_void_p(grads[name].data_ptr()), t.numel(),
+                                        C.c_float(lr), self._sh), "id_mlp_sgd")
+
+
 def gaussian_fill(which, seed, first, count, width, device=None, stream=None):
     """The counter-based Gaussian entries (which=1 Psi, 2 Omega) as a (count, width)
     FP32 CUDA tensor: row i holds G(first + i, 0:width)."""

@@ -127,3 +127,16 @@ def test_batch_count_limits(lib):
     assert lib.id_batch_run(None, None, None, None) == 1
     assert lib.id_batch_wait(None, None) == 1
     lib.id_batch_destroy(None)
+
+
+def test_network_calls_reject_bad_arguments_before_any_gpu_call(lib):
+    p = C.c_void_p(4096)
+    assert lib.id_mlp_forward(None, 10, 10, 8, p, p, p, p, p, p, p, None) == 1
+    assert lib.id_mlp_forward(p, 0, 10, 8, p, p, p, p, p, p, p, None) == 1
+    assert lib.id_mlp_forward(p, 10, 10, 0, p, p, p, p, p, p, p, None) == 1
+    assert lib.id_mlp_backward(p, 10, 10, 8, p, p, p, p, p, C.c_float(-1.0), p, p, p, p, p, p,
+                               None) == 1
+    assert lib.id_mlp_sgd(p, p, 0, C.c_float(0.1), None) == 1
+    assert lib.id_mlp_sgd(p, p, 10, C.c_float(float("nan")), None) == 1
+    assert lib.id_mlp_features(p, 100, 100, 10, 7, p, 5, C.c_float(1.0), p, None) == 1
+    assert lib.id_mlp_features(p, 99, 100, 10, 0, p, 5, C.c_float(1.0), p, None) == 1
