@@ -277,6 +277,20 @@ id_status id_batch_wait(id_batch* b, int32_t* kout_host);
 /* Synchronise the batch's stream and release everything it holds. */
 void id_batch_destroy(id_batch* b);
 
+/* ID of the streamed columns with the skeleton chosen among candidates
+ * (the learned proposal's): the pivoted QR of W(:, cand) gives J (pivot
+ * order, indices of the streamed columns, -1 past k_out), and P (k x n FP64
+ * row-major) is the least-squares fit of W on W(:, J) over all n streamed
+ * columns -- for a pivoted QR the same as R11^-1 R12 (Sec. 2.4) -- with
+ * P(:, J) = I exactly.  cand: ncand distinct column indices (host or
+ * device), 1 <= ncand <= n.  Outputs as id_factor (host or device;
+ * synchronises the stream).  Errors: ID_ERR_INVALID_ARG (NULL, ncand out of
+ * range, a candidate outside the streamed columns or repeated), ID_ERR_STATE
+ * (no columns yet), ID_ERR_RANK_DEFICIENT (fewer than k pivots above the
+ * rank tolerance among the candidates), ID_ERR_TIMEOUT, ID_ERR_CUDA. */
+id_status id_factor_restricted(id_sketch* h, const int32_t* cand, int32_t ncand, int32_t* J,
+                               double* P, int32_t* k_out);
+
 /* ---------------------------------------------------------------------
  * Learned skeleton proposal: the network's kernels.  No counterpart in the
  * paper (its conclusion motivates the ID as the selection of the most

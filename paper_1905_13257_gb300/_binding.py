@@ -74,6 +74,8 @@ SIGNATURES = {
     "id_sketch_reset": (C.c_int, [C.c_void_p]),
     "id_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "id_coarse_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "id_factor_restricted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                       C.c_void_p, C.POINTER(C.c_int32)]),
     "id_reconstruct_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                        C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                        C.POINTER(C.c_double)]),

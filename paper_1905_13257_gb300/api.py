@@ -128,6 +128,22 @@ class IdSketch:
         """Randomized ID from W = Psi A: returns (J, P, k_out)."""
         return self._factor(self.lib.id_factor, "id_factor", device)
 
+    def factor_restricted(self, cand, device="cuda"):
+        """ID with the skeleton chosen among the candidate columns cand
+        (id_factor_restricted): returns (J, P, k_out)."""
+        cand = torch.as_tensor(cand, dtype=torch.int32).contiguous().cpu()
+        n = self.n_seen()
+        dev = self.stream.device if device == "cuda" else torch.device("cpu")
+        J = torch.empty(self.k, dtype=torch.int32, device=dev)
+        P = torch.empty((self.k, n), dtype=torch.float64, device=dev)
+        kout = C.c_int32()
+        st = self.lib.id_factor_restricted(self.h, C.c_void_p(cand.data_ptr()), cand.numel(),
+                                           C.c_void_p(J.data_ptr()), C.c_void_p(P.data_ptr()),
+                                           C.byref(kout))
+        B.check(st, "id_factor_restricted", allow=(B.ID_ERR_RANK_DEFICIENT,))
+        self._keep = []
+        return J, P, kout.value
+
     def coarse_factor(self, device="cuda"):
         """Sub-sampled ID from the coarse rows: returns (J_c, P_c, k_out)."""
         return self._factor(self.lib.id_coarse_factor, "id_coarse_factor", device)

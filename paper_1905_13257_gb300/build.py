@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libidsketch.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "sketch_simt.cu", "sketch_tc.cu", "cpqr.cu", "coarse.cu", "recon.cu",
            "recon_tc.cu", "single_pass.cu", "noalloc.cu", "tma_host.cu", "batch.cu",
-           "mlp.cu", "gauss_table.cpp"]
+           "mlp.cu", "restricted.cu", "gauss_table.cpp"]
 
 
 def nvcc() -> str:

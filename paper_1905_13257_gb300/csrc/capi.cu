@@ -91,7 +91,7 @@ void free_all(id_sketch* h) {
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gvec, h->d_hvec, h->d_vh, h->d_vl,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
                   h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart,
-                  h->d_axis, h->d_Sc};
+                  h->d_axis, h->d_Sc, h->d_cand, h->d_fq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -370,6 +370,8 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   al.get(&h->d_J, (size_t)k);
   al.get(&h->d_colpos, (size_t)nm);
   al.get(&h->d_kout, 1);
+  al.get(&h->d_cand, (size_t)nm);
+  al.get(&h->d_fq, (size_t)l * k + k + (size_t)k * k);
   h->rec_blocks = 8 * h->nsm;
   al.get(&h->d_part, (size_t)3 * h->rec_blocks);
   al.get(&h->d_out3, 3);
@@ -466,6 +468,50 @@ id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out) {
   const int64_t n = h->n_seen;
   const int k = h->k;
   if ((s = copy_out(h, J, h->d_J, sizeof(int32_t) * k)) != ID_OK) return s;
+  if ((s = copy_out(h, P, h->d_P, sizeof(double) * k * n)) != ID_OK) return s;
+  int32_t kk = 0, dst = 0;
+  IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_kout, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaMemcpyAsync(&dst, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  if (dst) {
+    h->poisoned = true;
+    return ID_ERR_TIMEOUT;
+  }
+  if (k_out) *k_out = kk;
+  return kk < k ? ID_ERR_RANK_DEFICIENT : ID_OK;
+}
+
+id_status id_factor_restricted(id_sketch* h, const int32_t* cand, int32_t ncand, int32_t* J,
+                               double* P, int32_t* k_out) {
+  if (!h) return ID_ERR_INVALID_ARG;
+  if (h->poisoned) return ID_ERR_CUDA;
+  if (!cand || ncand < 1) return ID_ERR_INVALID_ARG;
+  id_status s = launch_pending(h);
+  if (s != ID_OK) return s;
+  const int64_t n = h->n_seen;
+  if (n == 0) return ID_ERR_STATE;
+  if (ncand > n) return ID_ERR_INVALID_ARG;
+  std::vector<int32_t> hc((size_t)ncand);
+  IDSK_CUDA(h, cudaMemcpyAsync(hc.data(), cand, sizeof(int32_t) * ncand, cudaMemcpyDefault,
+                               h->st));
+  IDSK_CUDA(h, cudaStreamSynchronize(h->st));
+  {
+    std::vector<int32_t> sorted(hc);
+    std::sort(sorted.begin(), sorted.end());
+    for (int32_t q = 0; q < ncand; ++q)
+      if (sorted[q] < 0 || sorted[q] >= n || (q > 0 && sorted[q] == sorted[q - 1]))
+        return ID_ERR_INVALID_ARG;   // outside the streamed columns, or repeated
+  }
+  const int k = h->k, l = h->l;
+  IDSK_CUDA(h, cudaMemcpyAsync(h->d_cand, hc.data(), sizeof(int32_t) * ncand,
+                               cudaMemcpyHostToDevice, h->st));
+  IDSK_CUDA(h, launch_gather_cols(h->d_W, h->n_max, l, h->d_cand, ncand, h->d_work, h->st));
+  IDSK_CUDA(h, launch_cpqr_small(h->d_work, l, ncand, ncand, k, ID_RANK_TOL_FACTOR, h->d_R,
+                                 h->d_J, h->d_colpos, h->d_kout, h->st));
+  IDSK_CUDA(h, launch_map_pivots(h->d_J, h->d_cand, h->d_kout, k, h->d_Jin, h->st));
+  IDSK_CUDA(h, launch_fixed_solve(h->d_W, h->n_max, l, (int)n, h->d_Jin, h->d_kout, k, h->d_fq,
+                                  h->d_P, h->st));
+  if ((s = copy_out(h, J, h->d_Jin, sizeof(int32_t) * k)) != ID_OK) return s;
   if ((s = copy_out(h, P, h->d_P, sizeof(double) * k * n)) != ID_OK) return s;
   int32_t kk = 0, dst = 0;
   IDSK_CUDA(h, cudaMemcpyAsync(&kk, h->d_kout, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));

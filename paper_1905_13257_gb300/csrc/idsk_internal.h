@@ -237,6 +237,8 @@ struct id_sketch {
   int* d_J = nullptr;         // k
   int* d_colpos = nullptr;    // n_max
   int* d_kout = nullptr;      // 1
+  int* d_cand = nullptr;      // n_max: candidate columns (id_factor_restricted)
+  double* d_fq = nullptr;     // l k + k + k k: reflectors, tau, R of W(:, J)
   // coarse workspace (allocated on first id_coarse_factor)
   double* d_V = nullptr;      // mc x k: reflectors as FP32 pairs (8 bytes each)
   double* d_F = nullptr;      // n_max x k
@@ -309,6 +311,12 @@ cudaError_t launch_single_pass_lift(const InterpGeom& g, int64_t m, int dtype, i
                                     cudaStream_t st);
 void gaussian_table_host(float* vals, uint16_t* bits);
 void count_launches(int64_t n);
+cudaError_t launch_gather_cols(const double* W, int64_t ldw, int l, const int* cand, int ncand,
+                               double* Wc, cudaStream_t st);
+cudaError_t launch_map_pivots(const int* Jc, const int* cand, const int* kout, int k, int* J,
+                              cudaStream_t st);
+cudaError_t launch_fixed_solve(const double* W, int64_t ldw, int l, int n, const int* J,
+                               const int* kout, int k, double* fq, double* P, cudaStream_t st);
 // Launch the sketch of every pending column window of the handle (capi.cu).
 id_status launch_pending(id_sketch* h);
 // Enqueue the randomized ID of the streamed columns (pivoted QR of W and the

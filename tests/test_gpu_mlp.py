@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import oracle.learned as L
 from synthetic import channel_field
 
@@ -95,3 +96,39 @@ def test_gpu_training_follows_the_oracle():
         assert np.max(np.abs(a - b)) <= 1e-3 * max(1.0, np.abs(b).max()), key
     last = L.bce_loss(net.forward(Xd).cpu().numpy().astype(np.float64), y64)
     assert last < 0.7 * first
+
+
+# ------------------------------------------- QR restricted to the candidates
+
+def test_factor_restricted_matches_the_oracle():
+    """id_factor_restricted against oracle.learned.restricted_id on the same
+    W: J identical (when the restricted pivots have a margin), P within 1e-9;
+    with every column a candidate it is the plain randomized ID."""
+    from paper_1905_13257_gb300 import IdError, IdSketch
+    grid, n, k, l = (16, 12, 16), 200, 12, 22
+    A = channel_field(grid, 3, n, seed=7, gap_k=k, dtype=torch.float32, device=DEV)
+    sk = IdSketch(m=A.shape[0], n_max=n, k=k, l=l, seed=9, dtype=torch.float32, want_Y=False)
+    sk.stream_columns(A)
+    W = sk.sketches()[0].cpu().numpy()
+    J0, P0, k0 = sk.factor(device="cpu")
+    assert k0 == k
+    rng = np.random.default_rng(2)
+    others = rng.choice(np.setdiff1d(np.arange(n), J0.numpy()), 12, replace=False)
+    cand = np.sort(np.concatenate([J0.numpy(), others]))
+    J, P, kk = sk.factor_restricted(cand, device="cpu")
+    Jo, Po, ko = L.restricted_id(W, cand, k)
+    assert kk == ko == k
+    _, _, _, margin = oracle.column_id(W[:, cand], k)
+    if margin >= 1e-4:
+        assert J.tolist() == Jo.tolist()
+        assert np.max(np.abs(P.numpy() - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
+    assert np.array_equal(P.numpy()[:, J.numpy()], np.eye(k))
+    # every column a candidate: the plain ID (P = R11^-1 R12)
+    J2, P2, k2 = sk.factor_restricted(np.arange(n), device="cuda")
+    assert k2 == k and J2.cpu().tolist() == J0.tolist()
+    assert np.max(np.abs(P2.cpu().numpy() - P0.numpy())) <= 1e-9 * max(1.0, P0.abs().max().item())
+    for bad in ([3, 3, 5], [0, n], [-1, 4]):
+        with pytest.raises(IdError) as e:
+            sk.factor_restricted(np.array(bad))
+        assert e.value.status == 1
+    sk.close()
