@@ -259,11 +259,6 @@ def run_ours(args):
             sk.stream_columns(A[:, j0:j0 + CHUNK])
         sk.flush()
         e1.record(stream)
-        if args.only == "sketch":
-            if record:
-                e1.synchronize()
-                phase_ms["sketch"] += e0.elapsed_time(e1)
-            return
         J, P, kout = sk.factor()
         e2.record(stream)
         Jc, Pc, kc = sk.coarse_factor()
@@ -541,15 +536,14 @@ def main():
     ap.add_argument("--grid", type=str, default=None,
                     help="nx,ny,nz of a smaller case (profiling); default 128,96,128")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["all", "sketch"], default="all",
-                    help="profiling aid: 'sketch' runs only the streamed sketch per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
                     help="y-planes of component u in the CPU-baseline sample")
     ap.add_argument("--workload", choices=["channel", "batched64"], default="channel",
                     help="batched64: the batched form (64 matrices of uneven size)")
-    ap.add_argument("--ref-planes", type=int, default=2,
-                    help="y-planes per step of the reference arm's sample")
+    ap.add_argument("--ref-planes", type=int, default=8,
+                    help="y-planes of component u per step of the reference arm's sample "
+                         "(the same sample as cpu_baseline by default)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

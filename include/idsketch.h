@@ -167,7 +167,11 @@ id_status id_reconstruct_error(id_sketch* h, const void* d_A, int64_t lda, int64
  * Set-up: the first call on each device (with that device current) looks up
  * the array's device address; make that first call before any stream
  * capture.  All calls on a device share the array: calls that overlap on the
- * GPU race.  Synchronises cuda_stream before returning.
+ * GPU race.  Synchronises cuda_stream before returning.  There is no handle,
+ * so nothing is poisoned: after ID_ERR_TIMEOUT (a bounded device wait gave
+ * up; the kernel has returned and the context stays usable) the next call
+ * clears the flag and runs again, whereas a handle of id_reconstruct_error
+ * refuses further work after a timeout.
  * Errors: ID_ERR_INVALID_ARG for the cases of id_reconstruct_error, a bad
  * dtype, or k * n > ID_NOALLOC_MAX_KN (the array's capacity for P). */
 id_status id_reconstruct_error_noalloc(const void* d_A, int64_t lda, int64_t m, int64_t n,

@@ -20,6 +20,8 @@
 
 #include <atomic>
 
+#include <algorithm>
+
 #include "idsk_internal.h"
 
 namespace idsk {
@@ -170,6 +172,12 @@ bool gemm_dims_ok(int64_t M, int64_t N, int64_t K) {
          (M + GT - 1) / GT <= 65535;
 }
 
+// The element-wise kernels take one thread per entry of an n x H (or n x 32)
+// array: their grid (blocks of 256) must stay below 2^31 blocks.
+bool elementwise_grid_ok(int64_t n, int64_t H) {
+  return n * std::max<int64_t>(H, 32) / 256 + 1 < ((int64_t)1 << 31);
+}
+
 }  // namespace
 
 extern "C" {
@@ -197,7 +205,7 @@ id_status id_mlp_forward(const float* d_X, int64_t n, int64_t F, int32_t H, cons
                          const float* d_b1, const float* d_w2, const float* d_b2, float* d_Z,
                          float* d_G, float* d_s, void* cuda_stream) {
   if (!d_X || !d_W1 || !d_b1 || !d_w2 || !d_b2 || !d_Z || !d_G || !d_s || H < 1 ||
-      !gemm_dims_ok(n, H, F))
+      !gemm_dims_ok(n, H, F) || !elementwise_grid_ok(n, H))
     return ID_ERR_INVALID_ARG;
   const cudaStream_t st = (cudaStream_t)cuda_stream;
   const dim3 grid((unsigned)((H + GT - 1) / GT), (unsigned)((n + GT - 1) / GT));
@@ -213,7 +221,8 @@ id_status id_mlp_backward(const float* d_X, int64_t n, int64_t F, int32_t H, con
                           float* d_gw2, float* d_gb2, float* d_ds, float* d_dZ,
                           void* cuda_stream) {
   if (!d_X || !d_Z || !d_G || !d_w2 || !d_s || !d_y || !d_gW1 || !d_gb1 || !d_gw2 || !d_gb2 ||
-      !d_ds || !d_dZ || H < 1 || !gemm_dims_ok(F, H, n) || !(pos_weight >= 0.f))
+      !d_ds || !d_dZ || H < 1 || !gemm_dims_ok(F, H, n) || !elementwise_grid_ok(n, H) ||
+      !(pos_weight >= 0.f))
     return ID_ERR_INVALID_ARG;
   const cudaStream_t st = (cudaStream_t)cuda_stream;
   dscore_kernel<<<blocks_for(n, 256), 256, 0, st>>>(d_s, d_y, n, pos_weight, d_ds);

@@ -1,5 +1,11 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times.
 
+Bars: sketches <= 1e-5 relative Frobenius (FP32) / 1e-12 (FP64); relative
+Frobenius errors within 1e-4 relative of the oracle's (FP32, no absolute
+term) / 1e-10 (FP64); J identical when the oracle's pivot margin is >= 1e-4,
+otherwise a valid skeleton whose error matches the oracle's ID (the margin is
+printed either way).
+
 * Full FP64 case: 32x32x32 grid x 3 components = 98,304 rows x 200 snapshots,
   k = 20, p = 10, seed 0, chunks of 32, coarse grid 4x: every output against
   the oracle.
@@ -16,6 +22,7 @@ import pytest
 import torch
 
 import oracle
+from margins import MARGIN, assert_valid_skeleton
 from synthetic import channel_field
 
 pytestmark = pytest.mark.gpu
@@ -53,15 +60,21 @@ def test_full_fp64_case_end_to_end():
     assert J.cpu().tolist() == Jo.tolist()
     assert np.max(np.abs(P.cpu().numpy() - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
     fo, mo = oracle.recon_error(An, Jo, Po)
-    assert abs(fro - fo) <= 1e-4 * fo + 1e-12
-    assert abs(mx - mo) <= 1e-4 * mo + 1e-12
+    assert abs(fro - fo) <= 1e-10 * fo
+    assert abs(mx - mo) <= 1e-10 * mo
     rows = oracle.coarse_rows(grid, nc, (4, 4, 4))
     assert np.array_equal(Ac.cpu().numpy(), An[rows])
     Jco, Pco, kco, mco = oracle.column_id(An[rows], k)
     assert kc == kco
-    if mco >= 1e-4:
+    print(f"full FP64 case: oracle pivot margins {margin:.2e} (sketch), {mco:.2e} (coarse)")
+    assert_valid_skeleton(Jc.cpu().numpy(), Pc.cpu().numpy(), kc, n)
+    if mco >= MARGIN:
         assert Jc.cpu().tolist() == Jco.tolist()
         assert np.max(np.abs(Pc.cpu().numpy() - Pco)) <= 1e-8 * max(1.0, np.abs(Pco).max())
+    else:
+        fco, _ = oracle.recon_error(An, Jco, Pco)
+        fcg, _ = oracle.recon_error(An, Jc.cpu().numpy(), Pc.cpu().numpy())
+        assert abs(fcg - fco) <= 1e-6 * fco
     sk.close()
 
 
@@ -107,44 +120,102 @@ def test_streamed_coarse_gather_exact(streamed_case):
     assert torch.equal(torch.as_tensor(c["Ac"], device="cuda"), c["A"][rows, :])
 
 
-def test_streamed_factor_against_oracle_qr(streamed_case):
-    c = streamed_case
-    Jo, Po, ko, margin = oracle.column_id(c["W"], c["k"])
-    assert c["kout"] == ko == c["k"]
-    assert np.array_equal(c["P"][:, c["J"]], np.eye(c["k"]))
-    if margin >= 1e-4:
-        assert c["J"].tolist() == Jo.tolist()
-        assert np.max(np.abs(c["P"] - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
-
-
-def test_streamed_coarse_factor_against_oracle_qr(streamed_case):
-    c = streamed_case
-    Jo, Po, ko, margin = oracle.column_id(c["Ac"].astype(np.float64), c["k"])
-    assert c["kc"] == ko
-    assert np.array_equal(c["Pc"][:, c["Jc"]], np.eye(c["kc"]))
-    if margin >= 1e-4:
-        assert c["Jc"].tolist() == Jo.tolist()
-        assert np.max(np.abs(c["Pc"] - Po)) <= 1e-8 * max(1.0, np.abs(Po).max())
-
-
-def test_streamed_reconstruction_error_exact_sum(streamed_case):
-    """The oracle's reconstruction error over all 4.7M rows, summed in row
-    chunks (each chunk an exact FP64 residual of the oracle)."""
-    c = streamed_case
-    A, J, P = c["A"], c["J"][: c["kout"]], c["P"][: c["kout"]]
+def _row_block_error(c, J, P, S=None, rb=262_144):
+    """The oracle's relative Frobenius and entry-wise errors of A ~ A(:, J) P
+    (or S P when S is given) over all rows of the streamed case, summed in
+    row blocks (each block an exact FP64 residual)."""
+    A = c["A"]
     ss_res = ss_a = 0.0
     rmax = 0.0
-    for r0 in range(0, c["m"], 262_144):
-        blk = A[r0:r0 + 262_144].cpu().double().numpy()
-        R = blk - blk[:, J] @ P
+    J = np.asarray(J, dtype=np.int64)
+    for r0 in range(0, c["m"], rb):
+        blk = A[r0:r0 + rb].cpu().double().numpy()
+        Ahat = (blk[:, J] if S is None else S[r0:r0 + rb]) @ P
+        R = blk - Ahat
         ss_res += float(np.sum(R * R))
         ss_a += float(np.sum(blk * blk))
         nz = blk != 0
         if np.any(nz):
             rmax = max(rmax, float(np.max(np.abs(R[nz]) / np.abs(blk[nz]))))
-    fo = np.sqrt(ss_res / ss_a)
-    assert abs(c["fro"] - fo) <= 1e-4 * fo + 2e-6
-    assert abs(c["mx"] - rmax) <= 1e-3 * rmax
+    return float(np.sqrt(ss_res / ss_a)), rmax
+
+
+def test_streamed_factor_against_oracle_qr(streamed_case):
+    c = streamed_case
+    Jo, Po, ko, margin = oracle.column_id(c["W"], c["k"])
+    print(f"streamed case: pivot margin of the QR of the GPU's W {margin:.2e}")
+    assert c["kout"] == ko == c["k"]
+    assert_valid_skeleton(c["J"], c["P"], c["kout"], c["n"])
+    if margin >= MARGIN:
+        assert c["J"].tolist() == Jo.tolist()
+        assert np.max(np.abs(c["P"] - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
+    else:   # within rounding of a tie: the same interpolation quality
+        assert np.max(np.abs(c["W"] - c["W"][:, c["J"]] @ c["P"])) <= \
+            1.0001 * np.max(np.abs(c["W"] - c["W"][:, Jo] @ Po)) + 1e-12
+
+
+def test_streamed_coarse_factor_against_oracle_qr(streamed_case):
+    c = streamed_case
+    Jo, Po, ko, margin = oracle.column_id(c["Ac"].astype(np.float64), c["k"])
+    print(f"streamed case: pivot margin of the coarse QR {margin:.2e}")
+    assert c["kc"] == ko
+    assert_valid_skeleton(c["Jc"], c["Pc"], c["kc"], c["n"])
+    if margin >= MARGIN:
+        assert c["Jc"].tolist() == Jo.tolist()
+        assert np.max(np.abs(c["Pc"] - Po)) <= 1e-8 * max(1.0, np.abs(Po).max())
+    else:   # within rounding of a tie: the same lifted error as the oracle's ID
+        fo, _ = _row_block_error(c, Jo, Po)
+        fg, _ = _row_block_error(c, c["Jc"][: c["kc"]], c["Pc"][: c["kc"]])
+        assert abs(fg - fo) <= 1e-6 * fo
+
+
+def test_streamed_randomized_id_against_full_oracle(streamed_case):
+    """Algorithm 4 run by the oracle on the whole bench workload (4,718,592 x
+    1000 FP32, l = 60, k = 50, seed 0): W = Psi A and Y = A Omega in FP64 over
+    row blocks, the pivoted QR of the 60 x 1000 W, P, and the relative error
+    of A ~ A(:, J) P over all rows.  Every entry of the GPU's W and Y, its J
+    (or, below the pivot margin, a valid skeleton), P and error against
+    these.  The oracle's error is the workload's "fixed relative error"."""
+    c = streamed_case
+    A, m, n, l, k, seed = c["A"], c["m"], c["n"], c["l"], c["k"], c["seed"]
+    Om = oracle.omega(n, l, seed)
+    Wo = np.zeros((l, n))
+    ey_num = ey_den = 0.0
+    rb = 262_144
+    for r0 in range(0, m, rb):
+        r1 = min(m, r0 + rb)
+        blk = A[r0:r1].cpu().double().numpy()
+        Wo += oracle.psi(l, 0, seed, rows=np.arange(r0, r1)) @ blk
+        Yo = blk @ Om
+        Yg = c["Y"][r0:r1].cpu().double().numpy()
+        ey_num += float(np.sum((Yg - Yo) ** 2))
+        ey_den += float(np.sum(Yo * Yo))
+    ew = rel(c["W"], Wo)
+    ey = float(np.sqrt(ey_num / ey_den))
+    Jo, Po, ko, margin = oracle.column_id(Wo, k)
+    fo, mo = _row_block_error(c, Jo, Po)
+    print(f"streamed case, oracle Alg. 4: rel. Frobenius error {fo:.6e}, entry-wise {mo:.4e}, "
+          f"pivot margin {margin:.2e}; GPU: W err {ew:.2e}, Y err {ey:.2e}, error {c['fro']:.6e}")
+    assert ew <= 1e-5 and ey <= 1e-5
+    assert c["kout"] == ko == k
+    assert_valid_skeleton(c["J"], c["P"], c["kout"], n)
+    if margin >= MARGIN:
+        assert c["J"].tolist() == Jo.tolist()
+        assert np.max(np.abs(c["P"] - Po)) <= 1e-3 * max(1.0, np.abs(Po).max())
+        assert abs(c["fro"] - fo) <= 1e-4 * fo
+    else:   # within rounding of a tie: a valid ID of A at the oracle's error
+        fg, _ = _row_block_error(c, c["J"], c["P"])   # (equal error: within 1.05x)
+        assert abs(c["fro"] - fg) <= 1e-4 * fg
+        assert fg <= 1.05 * fo
+
+
+def test_streamed_reconstruction_error_exact_sum(streamed_case):
+    """The oracle's reconstruction error of the GPU's own (J, P) over all
+    4.7M rows, summed in row chunks (each chunk an exact FP64 residual)."""
+    c = streamed_case
+    fo, rmax = _row_block_error(c, c["J"][: c["kout"]], c["P"][: c["kout"]])
+    assert abs(c["fro"] - fo) <= 1e-4 * fo
+    assert abs(c["mx"] - rmax) <= 1e-4 * rmax
 
 
 def test_streamed_single_pass_id(streamed_case):
@@ -165,17 +236,6 @@ def test_streamed_single_pass_id(streamed_case):
     M = osp.coarse_to_fine(grid, c["nc"], (4, 4, 4), coords, per)
     So = M @ c["Ac"].astype(np.float64)[:, c["Jc"][:kc]]
     assert rel(S, So) <= 1e-6
-    ss_res = ss_a = 0.0
-    rmax = 0.0
-    Pn = c["Pc"][:kc]
-    for r0 in range(0, c["m"], 262_144):
-        blk = A[r0:r0 + 262_144].cpu().double().numpy()
-        R = blk - So[r0:r0 + 262_144] @ Pn
-        ss_res += float(np.sum(R * R))
-        ss_a += float(np.sum(blk * blk))
-        nzm = blk != 0
-        if np.any(nzm):
-            rmax = max(rmax, float(np.max(np.abs(R[nzm]) / np.abs(blk[nzm]))))
-    fo = np.sqrt(ss_res / ss_a)
-    assert abs(fro - fo) <= 1e-4 * fo + 2e-6
-    assert abs(mx - rmax) <= 1e-3 * rmax
+    fo, rmax = _row_block_error(c, None, c["Pc"][:kc], S=So)
+    assert abs(fro - fo) <= 1e-4 * fo
+    assert abs(mx - rmax) <= 1e-4 * rmax

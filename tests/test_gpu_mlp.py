@@ -102,7 +102,8 @@ def test_gpu_training_follows_the_oracle():
 
 def test_factor_restricted_matches_the_oracle():
     """id_factor_restricted against oracle.learned.restricted_id on the same
-    W: J identical (when the restricted pivots have a margin), P within 1e-9;
+    W: J identical (the candidate draw gives the restricted pivots a margin),
+    P within 1e-9;
     with every column a candidate it is the plain randomized ID."""
     from paper_1905_13257_gb300 import IdError, IdSketch
     grid, n, k, l = (16, 12, 16), 200, 12, 22
@@ -112,16 +113,20 @@ def test_factor_restricted_matches_the_oracle():
     W = sk.sketches()[0].cpu().numpy()
     J0, P0, k0 = sk.factor(device="cpu")
     assert k0 == k
-    rng = np.random.default_rng(2)
-    others = rng.choice(np.setdiff1d(np.arange(n), J0.numpy()), 12, replace=False)
-    cand = np.sort(np.concatenate([J0.numpy(), others]))
+    # candidate sets: the first draw (from seed 2) whose restricted pivots have
+    # an oracle margin >= 1e-4, so that J is unique and always compared
+    for cseed in range(2, 34):
+        rng = np.random.default_rng(cseed)
+        others = rng.choice(np.setdiff1d(np.arange(n), J0.numpy()), 12, replace=False)
+        cand = np.sort(np.concatenate([J0.numpy(), others]))
+        if oracle.column_id(W[:, cand], k)[3] >= 1e-4:
+            break
+    assert oracle.column_id(W[:, cand], k)[3] >= 1e-4
     J, P, kk = sk.factor_restricted(cand, device="cpu")
     Jo, Po, ko = L.restricted_id(W, cand, k)
     assert kk == ko == k
-    _, _, _, margin = oracle.column_id(W[:, cand], k)
-    if margin >= 1e-4:
-        assert J.tolist() == Jo.tolist()
-        assert np.max(np.abs(P.numpy() - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
+    assert J.tolist() == Jo.tolist()
+    assert np.max(np.abs(P.numpy() - Po)) <= 1e-9 * max(1.0, np.abs(Po).max())
     assert np.array_equal(P.numpy()[:, J.numpy()], np.eye(k))
     # every column a candidate: the plain ID (P = R11^-1 R12)
     J2, P2, k2 = sk.factor_restricted(np.arange(n), device="cuda")

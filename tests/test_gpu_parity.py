@@ -3,18 +3,23 @@
 Tolerances (spec bars, and the arithmetic behind the rest):
   sketches W, Y   relative Frobenius <= 1e-5 for FP32 data (FP32-accurate
                   products, FP64 accumulation of W); <= 1e-12 for FP64 data
-  skeleton J      identical whenever the oracle's pivot margin is >= 1e-4
+  skeleton J      identical on gap inputs (their seeds give an oracle pivot
+                  margin >= 1e-4); elsewhere identical when the margin is
+                  >= 1e-4, otherwise a valid skeleton (P(:, J) = I) with the
+                  oracle's error
   P               from the same W: max |dP| <= 1e-9 * max(1, |P|) (FP64 QR on
                   both sides); end to end: bounded by the W error x cond(R11)
-  errors          |rel_fro - oracle| <= 1e-4 * oracle + atol, atol = 2e-6 for
-                  FP32 data (FP32 reconstruction: ~sqrt(k) * 2^-24 relative per
-                  entry), 1e-12 for FP64 data
+  rel. Frobenius  |e - e_oracle| <= 1e-4 * e_oracle for FP32 data (the
+  error           spec bar, no absolute term), 1e-10 * e_oracle for FP64
+  entry-wise      |e - e_oracle| <= 1e-4 * e_oracle (+ the FP32 rounding of
+  error           A_hat at the maximising entry, where A_ij is tiny)
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
+from margins import MARGIN, assert_valid_skeleton, sketch_seed_with_margin
 from synthetic import channel_field, low_rank_matrix, gaussian_matrix
 
 pytestmark = pytest.mark.gpu
@@ -25,6 +30,12 @@ DEV = "cuda"
 def _sk(**kw):
     from paper_1905_13257_gb300 import IdSketch
     return IdSketch(**kw)
+
+
+def err_tol(fo, dtype):
+    """Bar on the relative Frobenius error: 1e-4 relative for FP32 data
+    (the benchmark spec), 1e-10 relative for FP64 data."""
+    return (1e-4 if dtype == torch.float32 else 1e-10) * fo
 
 
 def rel(a, b):
@@ -116,23 +127,24 @@ def test_reset_and_restream():
 @pytest.mark.parametrize("grid,n,k,l", [((16, 12, 16), 120, 10, 20), ((8, 8, 8), 64, 20, 30),
                                         ((12, 12, 12), 200, 16, 16), ((12, 12, 12), 200, 16, 26)])
 def test_factor_parity_gap_input(dtype, grid, n, k, l):
+    """Gap inputs: J identical to the oracle's.  The sketch seed is the first
+    one (from 9) whose oracle pivot margin is >= 1e-4, so the comparison
+    always runs (the spectral gap makes the skeleton's span unique, the
+    margin makes the greedy pivot order unique)."""
     A = channel_field(grid, 3, n, seed=7, gap_k=k, dtype=dtype, device=DEV)
     m = A.shape[0]
-    sk = _sk(m=m, n_max=n, k=k, l=l, seed=9, dtype=dtype)
+    An = A.cpu().double().numpy()
+    seed, Wo, (Jo, Po, ko, margin) = sketch_seed_with_margin(An, k, l, range(9, 73))
+    sk = _sk(m=m, n_max=n, k=k, l=l, seed=seed, dtype=dtype)
     stream(sk, A, [32] * (n // 32) + ([n % 32] if n % 32 else []))
     J, P, kout = sk.factor()
     W = sk.sketches()[0].cpu().numpy()
-    An = A.cpu().double().numpy()
-    Wo, _ = oracle.sketch(An, oracle.psi(l, m, 9), oracle.omega(n, l, 9))
-    Jo, Po, ko, margin = oracle.column_id(Wo, k)
     assert kout == ko == k
     Pg = P.cpu().numpy()
     assert np.array_equal(Pg[:, J.cpu().numpy()], np.eye(k))
-    if margin < 1e-4:      # pivots within rounding of a tie: J is not unique
-        pytest.skip(f"oracle pivot margin {margin:.1e} < 1e-4")
     assert J.cpu().tolist() == Jo.tolist()
     # same W on both sides: FP64 QR agreement
-    Jw, Pw, _, _ = oracle.column_id(W, k)
+    Jw, Pw, _, mw = oracle.column_id(W, k)
     assert J.cpu().tolist() == Jw.tolist()
     assert np.max(np.abs(Pg - Pw)) <= 1e-9 * max(1.0, np.max(np.abs(Pw)))
     # end to end against the FP64 oracle
@@ -152,9 +164,14 @@ def test_factor_host_outputs_and_edge_ranks():
         Wo, _ = oracle.sketch(An[:, :n], oracle.psi(l, m, 1), oracle.omega(n, l, 1))
         Jo, Po, ko, margin = oracle.column_id(Wo, k)
         assert kout == ko
-        if margin >= 1e-4:
+        assert_valid_skeleton(J.numpy(), P.numpy(), kout, n)
+        if margin >= MARGIN:
             assert J.tolist()[:kout] == Jo.tolist()
-        assert np.max(np.abs(P.numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+            assert np.max(np.abs(P.numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+        else:   # pivot order within rounding of a tie: same error as the oracle's ID
+            fo, _ = oracle.recon_error(An[:, :n], Jo, Po)
+            fg, _ = oracle.recon_error(An[:, :n], J.numpy()[:kout], P.numpy()[:kout])
+            assert abs(fg - fo) <= 1e-6 * fo + 1e-14
         sk.close()
 
 
@@ -193,27 +210,32 @@ def test_zero_matrix():
                                              ((20, 9, 13), (4, 2, 3), 70, 12),
                                              ((8, 8, 8), (1, 1, 1), 40, 40)])
 def test_coarse_factor_parity(dtype, grid, stride, n, k):
+    """Gap inputs: J_c identical to the oracle's deterministic ID of A_c.  The
+    data seed is the first one (from 5) whose coarse matrix has an oracle
+    pivot margin >= 1e-4."""
     nc = 3
-    A = channel_field(grid, nc, n, seed=5, gap_k=k, dtype=dtype, device=DEV)
+    rows = oracle.coarse_rows(grid, nc, stride)
+    for dseed in range(5, 37):
+        A = channel_field(grid, nc, n, seed=dseed, gap_k=k, dtype=dtype, device=DEV)
+        An = A.cpu().double().numpy()
+        Jo, Po, ko, margin = oracle.column_id(An[rows], k)
+        if margin >= MARGIN:
+            break
+    assert margin >= MARGIN, f"no data seed gives a coarse pivot margin >= {MARGIN}"
     m = A.shape[0]
     sk = _sk(m=m, n_max=n, k=k, l=max(k, 16), seed=1, dtype=dtype, grid=grid, ncomp=nc,
              coarse_stride=stride, want_coarse=True, window_cols=64)
     stream(sk, A, [32] * (n // 32) + ([n % 32] if n % 32 else []))
     Jc, Pc, kout = sk.coarse_factor()
     Ac = sk.sketches()[2].cpu().numpy()
-    rows = oracle.coarse_rows(grid, nc, stride)
-    An = A.cpu().double().numpy()
     assert np.array_equal(Ac.astype(np.float64), An[rows])            # exact gather
-    Jo, Po, ko, margin = oracle.column_id(An[rows], k)
     assert kout == ko
-    if margin >= 1e-4:
-        assert Jc.cpu().tolist()[:kout] == Jo.tolist()
-        assert np.max(np.abs(Pc.cpu().numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+    assert Jc.cpu().tolist()[:kout] == Jo.tolist()
+    assert np.max(np.abs(Pc.cpu().numpy()[:kout] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
     # lifted error (eq. eq:coarseregA) through the fused error pass
     fro, mx = sk.reconstruct_error(A, Jc[:kout], Pc[:kout])
     fo, mo = oracle.recon_error(An, Jo, Po)
-    atol = 2e-6 if dtype == torch.float32 else 1e-12
-    assert abs(fro - fo) <= 1e-4 * fo + atol
+    assert abs(fro - fo) <= err_tol(fo, dtype)
     sk.close()
 
 
@@ -233,9 +255,9 @@ def test_coarse_rank_deficient():
 
 # ------------------------------------------------------------- error pass
 
-@pytest.mark.parametrize("dtype,atol", [(torch.float32, 2e-6), (torch.float64, 1e-12)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("m,n,k", [(6000, 100, 10), (4097, 33, 1), (64 * 7 + 5, 250, 64)])
-def test_recon_error_parity(dtype, atol, m, n, k):
+def test_recon_error_parity(dtype, m, n, k):
     A = gaussian_matrix(m, n, seed=m, dtype=dtype, device=DEV)
     A = A + low_rank_matrix(m, n, 4, seed=1, dtype=dtype, device=DEV) * 10
     A[5, 3] = 0.0   # skipped by the entry-wise metric
@@ -245,11 +267,29 @@ def test_recon_error_parity(dtype, atol, m, n, k):
     sk = _sk(m=m, n_max=n, k=min(k, 64), l=64, seed=0, dtype=dtype)
     fro, mx = sk.reconstruct_error(A, J, P)
     fo, mo = oracle.recon_error(A.cpu().double().numpy(), J.numpy(), P.numpy())
-    assert abs(fro - fo) <= 1e-4 * fo + atol
-    assert abs(mx - mo) <= 1e-4 * mo + atol
+    assert abs(fro - fo) <= err_tol(fo, dtype)
+    assert abs(mx - mo) <= err_tol(mo, dtype)
     # device-resident J and P give the same numbers
     fro2, mx2 = sk.reconstruct_error(A, J.to(DEV), P.to(DEV))
     assert fro2 == fro and mx2 == mx
+    sk.close()
+
+
+@pytest.mark.parametrize("k", [10, 50])
+def test_recon_error_small_residual_fp32(k):
+    """The spec bar where it is hardest for FP32: a reconstruction
+    whose relative error is about 1e-3 (the residual cancels about 10 bits
+    of A), skeleton and P from the oracle's ID of the exact data."""
+    grid, n = (16, 12, 16), 200
+    A = channel_field(grid, 3, n, seed=3, gap_k=k, dtype=torch.float32, device=DEV)
+    An = A.cpu().double().numpy()
+    Jo, Po, ko, _ = oracle.column_id(An, k)
+    fo, mo = oracle.recon_error(An, Jo, Po)
+    assert 1e-4 < fo < 1e-2
+    sk = _sk(m=A.shape[0], n_max=n, k=k, l=64, seed=0, dtype=torch.float32)
+    fro, mx = sk.reconstruct_error(A, torch.as_tensor(Jo, dtype=torch.int32),
+                                   torch.as_tensor(Po))
+    assert abs(fro - fo) <= 1e-4 * fo
     sk.close()
 
 

@@ -4,7 +4,7 @@ A ~ M A_c(:, J_c) P_c, against the oracle's interpolation operator.
 Bars: the lifted skeleton S = M A_c(:, J_c) within 1e-6 relative Frobenius
 for FP32 data (FP32 interpolation: weights and 8-term sums rounded to FP32)
 and 1e-13 for FP64; the errors as for the plain ID error pass
-(|e - e_oracle| <= 1e-4 e_oracle + atol, atol 2e-6 FP32, 1e-12 FP64).
+(|e - e_oracle| <= 1e-4 e_oracle for FP32 data, 1e-10 e_oracle for FP64).
 """
 import numpy as np
 import pytest
@@ -35,14 +35,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("dtype,stol,atol", [(torch.float32, 1e-6, 2e-6),
-                                              (torch.float64, 1e-13, 1e-12)])
+@pytest.mark.parametrize("dtype,stol,etol", [(torch.float32, 1e-6, 1e-4),
+                                              (torch.float64, 1e-13, 1e-10)])
 @pytest.mark.parametrize("grid,nc,stride,n,k", [
     ((20, 13, 12), 3, (4, 4, 3), 150, 12),   # ragged tails in y and z; m >= 128: tensor cores (FP32)
     ((9, 7, 5), 2, (2, 3, 2), 40, 6),        # small m: SIMT error pass
     ((16, 12, 16), 3, (4, 4, 4), 300, 40),   # several 256-column tiles
 ])
-def test_single_pass_lift_and_error(dtype, stol, atol, grid, nc, stride, n, k):
+def test_single_pass_lift_and_error(dtype, stol, etol, grid, nc, stride, n, k):
     A = channel_field(grid, nc, n, seed=8, dtype=dtype, device=DEV)
     m = A.shape[0]
     sk = _sk(m=m, n_max=n, k=k, l=k + 8, seed=2, dtype=dtype, grid=grid, ncomp=nc,
@@ -61,8 +61,8 @@ def test_single_pass_lift_and_error(dtype, stol, atol, grid, nc, stride, n, k):
     So = M @ An[rows][:, Jn]
     assert rel(S.cpu().numpy(), So) <= stol
     fo, mo = osp.single_pass_error(An, So, Pc[:kc].cpu().numpy())
-    assert abs(fro - fo) <= 1e-4 * fo + atol
-    assert abs(mx - mo) <= 1e-4 * mo + atol * mo
+    assert abs(fro - fo) <= etol * fo
+    assert abs(mx - mo) <= etol * mo
     # two calls in a row give the same numbers (the skeleton buffer is rebuilt)
     assert sk.single_pass_error(A, Jc[:kc], Pc[:kc]) == (fro, mx)
     sk.close()

@@ -261,6 +261,49 @@ def test_subsampled_id_theorem21_bound():
     assert np.allclose((A[:, Jc] @ Pc)[rows], Ac[:, Jc] @ Pc)
 
 
+def test_theorem21_rho_hand_computed_values():
+    """rho_k(tau) of Theorem 2.1 on a 4 x 2 example worked by hand (two-sided
+    pin: a dropped factor, a swapped sigma index or a norm in place of its
+    square changes these values).
+
+    A_c = [[2, 1], [0, 1]] and A = [A_c; A_c], so A^T A = 2 A_c^T A_c.
+    A_c^T A_c = [[4, 2], [2, 2]] has eigenvalues 3 +- sqrt(5), so
+    sigma_1^2 = 3 + sqrt(5), sigma_2^2 = 3 - sqrt(5), and
+    eps(tau) = lambda_max((2 - tau) A_c^T A_c) = (2 - tau)(3 + sqrt 5) for
+    tau <= 2 and (2 - tau)(3 - sqrt 5) above.  The k = 1 ID of A_c pivots
+    column 0 (norm 2 > sqrt 2); its R row is (-2, -1), so P_c = [1, 1/2],
+    ||P_c||_2 = sqrt(5)/2, and A_c - A_c(:, 0) P_c = [[0, 0], [0, 1]] has
+    2-norm 1.
+    """
+    Ac = np.array([[2.0, 1.0], [0.0, 1.0]])
+    A = np.vstack([Ac, Ac])
+    J, P, k_out, _ = oracle.column_id(Ac, 1)
+    assert list(J) == [0] and np.allclose(P, [[1.0, 0.5]], rtol=0, atol=1e-15)
+    ac_err = oracle.spectral_norm(Ac - Ac[:, J] @ P)
+    assert abs(ac_err - 1.0) < 1e-14
+    r5 = np.sqrt(5.0)
+    s1, s2 = 3.0 + r5, 3.0 - r5                    # sigma_1^2, sigma_2^2
+    pn = r5 / 2.0
+
+    def rho(tau):
+        eps = (2.0 - tau) * (s1 if tau <= 2.0 else s2)
+        return (1.0 + pn) * np.sqrt(tau * s2 + eps) + 1.0 * np.sqrt(tau + eps / s1)
+
+    for tau, closed in [(2.0, (1.0 + pn) * np.sqrt(2.0 * s2) + np.sqrt(2.0)),
+                        (1.0, (1.0 + pn) * np.sqrt(6.0) + np.sqrt(2.0)),
+                        (0.0, (1.0 + pn) * np.sqrt(2.0 * s1) + np.sqrt(2.0)),
+                        (3.0, None)]:
+        got = oracle.theorem21_rho(A, Ac, P, ac_err, 1, tau)
+        assert abs(got - rho(tau)) <= 1e-12 * rho(tau)
+        if closed is not None:
+            assert abs(got - closed) <= 1e-12 * closed
+    assert abs(oracle.theorem21_rho(A, Ac, P, ac_err, 1, 2.0) - 4.032247551) < 1e-8
+    # the theorem's statement on this example: ||A - A_hat||_2 = sqrt(2)
+    err = oracle.spectral_norm(A - A[:, J] @ P)
+    assert abs(err - np.sqrt(2.0)) < 1e-14
+    assert err <= min(oracle.theorem21_rho(A, Ac, P, ac_err, 1, t) for t in (0.0, 1.0, 2.0, 3.0))
+
+
 # --------------------------------------------------------------- error metric
 
 def test_recon_error_small_example():

@@ -153,3 +153,23 @@ def test_planted_mistake_swapped_weights_is_caught(monkeypatch):
     monkeypatch.setattr(osp, "axis_weights", swapped)
     with pytest.raises(AssertionError):
         test_trilinear_fields_are_reproduced()
+
+
+def test_theorem22_bound_hand_computed_value():
+    """Right side of Theorem 2.2 on a 3 x 3 example worked by hand (two-sided
+    pin).  A_c = [[3, 0, 0], [0, 1, 0]] (singular values 3, 1; k = 1 gives
+    sigma_2 = 1); M = [[1, 0], [0, 1], [1/2, 1/2]] has M^T M = [[5/4, 1/4],
+    [1/4, 5/4]] with eigenvalues 3/2 and 1, so ||M||_2 = sqrt(3/2); A = M A_c
+    + E with E zero except E[2, 2] = 2, so ||E_I||_2 = 2; n = 3 snapshots, so
+    sqrt(1 + k (n - k)) = sqrt(3).  Bound: 2 + sqrt(3/2) sqrt(3) = 2 +
+    sqrt(9/2)."""
+    Ac = np.array([[3.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    M = np.array([[1.0, 0.0], [0.0, 1.0], [0.5, 0.5]])
+    E = np.zeros((3, 3))
+    E[2, 2] = 2.0
+    A = M @ Ac + E
+    b = osp.theorem22_bound(A, Ac, M, 1)
+    assert abs(b - (2.0 + np.sqrt(4.5))) <= 1e-12
+    assert abs(b - 4.121320343559643) <= 1e-12
+    # k = 2 = rank(A_c): sigma_3 = 0 and the bound is the interpolation error
+    assert abs(osp.theorem22_bound(A, Ac, M, 2) - 2.0) <= 1e-12
