@@ -526,6 +526,125 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------- learned proposal
+
+def run_learned(args):
+    """The learned skeleton proposal on the bench's snapshot stream: train the
+    network on the plain ID's skeletons of 200 earlier 512-snapshot windows,
+    then compare, on later windows, the plain randomized ID with the learned
+    proposal (2k candidates, restricted pivoted QR, fallback at 1.05x the
+    plain error): errors, fallback rate, candidate recall, and the time of
+    one window's ID (sketch + QR + error pass) of each form."""
+    import numpy as np
+    import torch
+
+    from paper_1905_13257_gb300 import IdSketch, load
+    from paper_1905_13257_gb300.learned import (LearnedProposal, bce, compare_on_window,
+                                                plain_skeleton)
+    from synthetic.channel import channel_field, snapshot_step
+
+    load()
+    torch.cuda.set_device(0)
+    grid = tuple(int(x) for x in args.grid.split(",")) if args.grid else GRID
+    nwin, ntrain, nheld = 512, args.train_windows, args.held_windows
+    m = NCOMP * grid[0] * grid[1] * grid[2]
+    dt = snapshot_step(NSNAP)
+
+    def window(w):
+        return channel_field(grid, NCOMP, nwin, seed=SEED, dtype=torch.float32, device="cuda",
+                             first=w * nwin, dt=dt)
+
+    stride = (grid[0] // 16, grid[1] // 16, grid[2] // 16)
+    sk = IdSketch(m, nwin, K_RANK, L_SKETCH, seed=SEED, dtype=torch.float32, want_Y=False)
+    prop = LearnedProposal(grid, K_RANK, stride=stride, seed=1)
+    t0 = time.perf_counter()
+    data = []
+    for w in range(ntrain):
+        A = window(w)
+        J, _ = plain_skeleton(sk, A)
+        y = torch.zeros(nwin, dtype=torch.float32, device="cuda")
+        y[J.long()] = 1.0
+        data.append((prop.features(A), y))
+        del A
+    t_data = time.perf_counter() - t0
+    pw = (nwin - K_RANK) / K_RANK
+    losses = []
+    t0 = time.perf_counter()
+    for _ in range(args.epochs):
+        tot = 0.0
+        for X, y in data:
+            s = prop.train_step(X, y, lr=args.lr, pos_weight=pw)
+            tot += bce(s.cpu().numpy(), y.cpu().numpy(), pw)
+        losses.append(tot / len(data))
+    prop.net.check()
+    t_train = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    rows = []
+    for w in range(ntrain, ntrain + nheld):
+        rows.append(compare_on_window(prop, sk, window(w), rng))
+    # one window's ID, each form: stream (sketch) + QR (+ proposal) + error pass
+    A = window(ntrain)
+    X = prop.features(A)
+
+    def plain_form():
+        sk.reset()
+        for j0 in range(0, nwin, CHUNK):
+            sk.stream_columns(A[:, j0:j0 + CHUNK])
+        J, P, kout = sk.factor()
+        return sk.reconstruct_error(A, J[:kout], P[:kout])
+
+    def learned_form():
+        sk.reset()
+        for j0 in range(0, nwin, CHUNK):
+            sk.stream_columns(A[:, j0:j0 + CHUNK])
+        cand = prop.propose(prop.features(A))
+        J, P, kout = sk.factor_restricted(cand)
+        return sk.reconstruct_error(A, J[:kout], P[:kout])
+
+    times = {}
+    for name, fn in (("plain", plain_form), ("learned", learned_form)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / args.steps
+    wbytes = 4.0 * m * nwin
+    ratio_l = [r["err_learned"] / r["err_plain"] for r in rows]
+    ratio_r = [r["err_random"] / r["err_plain"] for r in rows]
+    line = {
+        "metric": "learned skeleton proposal vs plain randomized ID at equal error (<= 1.05x)",
+        "value": wbytes / (times["learned"] / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": times["learned"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic channel-field stream (seeded), windows of 512 snapshots",
+        "config": {"workload": f"learned proposal: {ntrain} training + {nheld} held-out windows "
+                               f"of {grid[0]}x{grid[1]}x{grid[2]}x{NCOMP} = {m} rows x {nwin} "
+                               f"snapshots FP32, k={K_RANK}, l={L_SKETCH}, 2k candidates, "
+                               f"4096 features, 256 hidden units, BF16 products",
+                   "epochs": args.epochs, "lr": args.lr},
+        "plain_ms_per_window": times["plain"],
+        "plain_GBs": wbytes / (times["plain"] / 1e3) / 1e9,
+        "training": {"loss_per_epoch": losses, "data_s": t_data, "train_s": t_train},
+        "held_out": {"err_ratio_learned": ratio_l, "err_ratio_random": ratio_r,
+                     "proposal_used": int(sum(r["use_learned"] for r in rows)),
+                     "windows": len(rows),
+                     "recall_learned": float(np.mean([r["recall_learned"] for r in rows])),
+                     "recall_random": float(np.mean([r["recall_random"] for r in rows])),
+                     "err_plain": [r["err_plain"] for r in rows],
+                     "qr_plain_ms": 1e3 * float(np.median([r["qr_plain_s"] for r in rows])),
+                     "proposal_and_qr_ms":
+                         1e3 * float(np.median([r["proposal_and_qr_s"] for r in rows]))},
+    }
+    print(json.dumps(line), flush=True)
+    sk.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -539,8 +658,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
                     help="y-planes of component u in the CPU-baseline sample")
-    ap.add_argument("--workload", choices=["channel", "batched64"], default="channel",
-                    help="batched64: the batched form (64 matrices of uneven size)")
+    ap.add_argument("--workload", choices=["channel", "batched64", "learned"],
+                    default="channel",
+                    help="batched64: the batched form (64 matrices of uneven size); "
+                         "learned: the learned skeleton proposal (training + comparison)")
+    ap.add_argument("--train-windows", type=int, default=200)
+    ap.add_argument("--held-windows", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=0.05)
     ap.add_argument("--ref-planes", type=int, default=8,
                     help="y-planes of component u per step of the reference arm's sample "
                          "(the same sample as cpu_baseline by default)")
@@ -551,6 +676,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -318,22 +318,38 @@ id_status id_mlp_features(const void* d_A, int64_t lda, int64_t m, int64_t n, in
                           void* cuda_stream);
 
 /* Forward pass on n feature rows X (n x F): Z = X W1 + b1 (n x H), G =
- * gelu(Z), s = G w2 + b2 (n).  W1: F x H; b1, w2: H; b2: 1 value. */
+ * gelu(Z), s = G w2 + b2 (n).  W1: F x H; b1, w2: H; b2: 1 value.  The
+ * product X W1 runs on the tensor cores with bfloat16 operands (X and W1 are
+ * rounded to bfloat16 as they are staged: bfloat16 weights) and FP32
+ * accumulation; the bias, GELU and score are FP32. */
 id_status id_mlp_forward(const float* d_X, int64_t n, int64_t F, int32_t H, const float* d_W1,
                          const float* d_b1, const float* d_w2, const float* d_b2, float* d_Z,
                          float* d_G, float* d_s, void* cuda_stream);
 
 /* Gradients of the loss for targets y (n values in {0, 1}) from a forward
  * pass's Z, G and s: gW1 (F x H), gb1 (H), gw2 (H), gb2 (1).  Scratch: ds (n),
- * dZ (n x H). */
+ * dZ (n x H).  gW1 = X^T dZ runs on the tensor cores (bfloat16 operands, FP32
+ * accumulation); the other gradients are FP32. */
 id_status id_mlp_backward(const float* d_X, int64_t n, int64_t F, int32_t H, const float* d_Z,
                           const float* d_G, const float* d_w2, const float* d_s,
                           const float* d_y, float pos_weight, float* d_gW1, float* d_gb1,
                           float* d_gw2, float* d_gb2, float* d_ds, float* d_dZ,
                           void* cuda_stream);
 
-/* Gradient step p -= lr g over count values. */
+/* Gradient step p -= lr g over count values (FP32 master parameters). */
 id_status id_mlp_sgd(float* d_p, const float* d_g, int64_t count, float lr, void* cuda_stream);
+
+/* The learned proposal's candidates: the count columns of highest score s
+ * (n device values; ties to the lower column index; NaN below every number),
+ * written to d_cand (count device int32) in increasing column order.
+ * 1 <= count <= n <= 4096. */
+id_status id_mlp_propose(const float* d_s, int64_t n, int32_t count, int32_t* d_cand,
+                         void* cuda_stream);
+
+/* Synchronises cuda_stream and reports whether a bounded device wait of the
+ * tensor-core products gave up since the last check (ID_ERR_TIMEOUT; the
+ * affected outputs hold NaN, the flag is cleared) or ID_OK. */
+id_status id_mlp_check(void* cuda_stream);
 
 /* Borrow the device buffers of the sketch (valid until reset/destroy):
  *   W  l x n_max FP64, row-major (entry (s, j) at W[s*n_max + j])

@@ -15,7 +15,10 @@ here:
   ``coarse_rows``), 4096 values, multiplied by one global scale (the inverse
   RMS of the training features) so that the inputs are O(1);
 * network: s = w2 . gelu(x W1 + b1) + b2 with 256 hidden units and the exact
-  GELU, gelu(z) = z Phi(z) (Phi the standard normal CDF);
+  GELU, gelu(z) = z Phi(z) (Phi the standard normal CDF); its two dense
+  products (x W1 and the W1 gradient X^T dZ) take bfloat16 operands with
+  exact accumulation here (``product_round=bf16_operands``), the precision
+  of the GPU's tensor-core products (which accumulate in FP32);
 * training target: y_j = 1 when column j is in the skeleton the plain
   randomized ID picked on that window, else 0; loss: the mean binary cross
   entropy of sigmoid(s) against y, positives optionally weighted;
@@ -89,10 +92,22 @@ def init_params(F, H=HIDDEN, seed=0):
             "b2": 0.0}
 
 
-def forward(X, p):
-    """Scores s (n) and the cache (Z, G) of the hidden layer."""
+def bf16_operands(M):
+    """Every value rounded to the nearest bfloat16 (ties to even): the
+    operand precision of the network's two dense products on the GPU."""
+    from .rng import bf16_round_f64
+    return bf16_round_f64(np.asarray(M, dtype=np.float64))[0]
+
+
+def forward(X, p, product_round=None):
+    """Scores s (n) and the cache (Z, G) of the hidden layer.
+
+    product_round (e.g. bf16_operands) is applied to both operands of the
+    product X W1 (bfloat16 weights and features, exact FP64 accumulation);
+    None keeps them as they are."""
     X = np.asarray(X, dtype=np.float64)
-    Z = X @ p["W1"] + p["b1"]
+    r = (lambda M: M) if product_round is None else product_round
+    Z = r(X) @ r(p["W1"]) + p["b1"]
     G = gelu(Z)
     s = G @ p["w2"] + p["b2"]
     return s, (Z, G)
@@ -118,11 +133,15 @@ def bce_loss(s, y, pos_weight=1.0):
     return float(np.mean(pos_weight * y * softplus(-s) + (1.0 - y) * softplus(s)))
 
 
-def backward(X, y, p, pos_weight=1.0):
-    """Gradients of bce_loss(forward(X, p), y) with respect to every parameter."""
+def backward(X, y, p, pos_weight=1.0, product_round=None):
+    """Gradients of bce_loss(forward(X, p), y) with respect to every parameter.
+
+    product_round, as in forward, also rounds both operands of the product
+    X^T dZ that gives the W1 gradient."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    s, (Z, G) = forward(X, p)
+    r = (lambda M: M) if product_round is None else product_round
+    s, (Z, G) = forward(X, p, product_round)
     n = X.shape[0]
     sg = sigmoid(s)
     # d/ds of w y softplus(-s) + (1 - y) softplus(s) = -w y (1 - sg) + (1 - y) sg
@@ -130,7 +149,7 @@ def backward(X, y, p, pos_weight=1.0):
     gw2 = G.T @ ds
     gb2 = float(np.sum(ds))
     dZ = np.outer(ds, p["w2"]) * gelu_grad(Z)
-    gW1 = X.T @ dZ
+    gW1 = r(X).T @ r(dZ)
     gb1 = np.sum(dZ, axis=0)
     return {"W1": gW1, "b1": gb1, "w2": gw2, "b2": gb2}
 

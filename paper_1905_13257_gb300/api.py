@@ -129,9 +129,11 @@ class IdSketch:
         return self._factor(self.lib.id_factor, "id_factor", device)
 
     def factor_restricted(self, cand, device="cuda"):
-        """ID with the skeleton chosen among the candidate columns cand
-        (id_factor_restricted): returns (J, P, k_out)."""
-        cand = torch.as_tensor(cand, dtype=torch.int32).contiguous().cpu()
+        """ID with the skeleton chosen among the candidate columns cand (host
+        or CUDA int32 indices; id_factor_restricted): returns (J, P, k_out)."""
+        if not (torch.is_tensor(cand) and cand.is_cuda):
+            cand = torch.as_tensor(cand, dtype=torch.int32).cpu()
+        cand = cand.to(torch.int32).contiguous()
         n = self.n_seen()
         dev = self.stream.device if device == "cuda" else torch.device("cpu")
         J = torch.empty(self.k, dtype=torch.int32, device=dev)
@@ -303,7 +305,8 @@ def mlp_features(A, rows, scale=1.0, stream=None):
 
 class Mlp:
     """The learned proposal's network on the GPU (id_mlp_*): s = w2 .
-    gelu(x W1 + b1) + b2, parameters as FP32 CUDA tensors (W1: F x H)."""
+    gelu(x W1 + b1) + b2, parameters as FP32 CUDA tensors (W1: F x H; the
+    products use them rounded to bfloat16, with FP32 accumulation)."""
 
     def __init__(self, params, device="cuda", stream=None):
         self.lib = B.load()
@@ -343,6 +346,11 @@ class Mlp:
                                          p(g["W1"]), p(g["b1"]), p(g["w2"]), p(g["b2"]), p(ds),
                                          p(dZ), self._sh), "id_mlp_backward")
         return g
+
+    def check(self):
+        """Synchronise the stream and raise if a tensor-core product's bounded
+        wait gave up since the last check (id_mlp_check)."""
+        B.check(self.lib.id_mlp_check(self._sh), "id_mlp_check")
 
     def step(self, grads, lr):
         """SGD: every parameter -= lr * its gradient."""

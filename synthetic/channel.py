@@ -82,8 +82,17 @@ def _chebyshev(q, y):
     return np.cos(q * np.arccos(np.clip(y, -1.0, 1.0)))
 
 
-def factors(grid, ncomp, n, seed, gap_k=None, device="cpu"):
-    """FP64 factors S (m x 128) and T (128 x n) with A_clean = S @ T (unit RMS)."""
+def snapshot_step(n):
+    """Time between snapshots when n snapshots span SPAN flow-through times."""
+    return SPAN * LX / (U_C * max(n, 1))
+
+
+def factors(grid, ncomp, n, seed, gap_k=None, device="cpu", first=0, dt=None):
+    """FP64 factors S (m x 128) and T (128 x n) with A_clean = S @ T (unit RMS).
+
+    Snapshot s is taken at time (first + s) * dt, dt = snapshot_step(n) by
+    default; a later window of one flow (same seed) takes first > 0 and the
+    dt of the whole stream.  The RMS scale is that of the window."""
     nx, ny, nz = (int(g) for g in grid)
     if not 1 <= ncomp <= 3:
         raise ValueError("ncomp must be 1, 2 or 3")
@@ -97,7 +106,8 @@ def factors(grid, ncomp, n, seed, gap_k=None, device="cpu"):
     y = wall_normal_points(ny)
     m = ncomp * ny * nz * nx
     S = torch.empty((m, 2 * len(md)), dtype=f64, device=dev)
-    t = torch.arange(n, dtype=f64, device=dev) * (SPAN * LX / (U_C * max(n, 1)))
+    step = snapshot_step(n) if dt is None else float(dt)
+    t = (float(first) + torch.arange(n, dtype=f64, device=dev)) * step
     T = torch.empty((2 * len(md), n), dtype=f64, device=dev)
     plane = ny * nz * nx
     for mi, (ax, az, amp, q) in enumerate(md):
@@ -123,13 +133,16 @@ def factors(grid, ncomp, n, seed, gap_k=None, device="cpu"):
 
 
 def channel_field(grid, ncomp, n, seed, noise=1e-6, gap_k=None, dtype=torch.float32,
-                  device="cpu", col_chunk=64):
-    """Snapshot matrix A (m x n, column-major torch view) on ``device``."""
-    S, T = factors(grid, ncomp, n, seed, gap_k=gap_k, device=device)
+                  device="cpu", col_chunk=64, first=0, dt=None):
+    """Snapshot matrix A (m x n, column-major torch view) on ``device``.
+
+    first / dt select a window of a longer stream of the same flow (see
+    ``factors``); each window draws its own noise."""
+    S, T = factors(grid, ncomp, n, seed, gap_k=gap_k, device=device, first=first, dt=dt)
     m = S.shape[0]
     At = torch.empty((n, m), dtype=dtype, device=S.device)
     gen = torch.Generator(device=S.device)
-    gen.manual_seed(int(seed) * 7919 + 3)
+    gen.manual_seed(int(seed) * 7919 + 3 + 1_000_003 * int(first))
     St = S.T.contiguous()
     for j0 in range(0, n, col_chunk):
         j1 = min(n, j0 + col_chunk)

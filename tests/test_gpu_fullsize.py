@@ -11,11 +11,11 @@ printed either way).
   the oracle.
 * Streamed FP32 case: 128x96x128 x 3 = 4,718,592 rows x 1000 snapshots
   (18.9 GB), chunks of 32 aggregated into one window, l = 60, k = 50, coarse
-  4x: sampled columns of W and rows of Y against the oracle's one-by-one
-  products, the exact coarse gather, the pivoted QRs against the oracle on
-  the same (validated) inputs, and the reconstruction errors of the
-  sub-sampled and the single-pass ID against the oracle's exact sums taken
-  over row chunks.
+  4x: the oracle's Algorithm 4 on the whole matrix (every entry of W and Y,
+  the QR of its own W, its error), the exact coarse gather, the pivoted QRs
+  against the oracle on the same inputs, and the errors of the randomized,
+  sub-sampled and single-pass IDs against the oracle's exact sums over all
+  rows, all from one pass of the oracle over row blocks.
 """
 import numpy as np
 import pytest
@@ -95,23 +95,86 @@ def streamed_case():
     out = dict(sk=sk, A=A, grid=grid, nc=nc, n=n, k=k, l=l, seed=seed, m=m, J=J.cpu().numpy(),
                P=P.cpu().numpy(), kout=kout, Jc=Jc.cpu().numpy(), Pc=Pc.cpu().numpy(), kc=kc,
                fro=fro, mx=mx, W=W.cpu().numpy().copy(), Y=Y, Ac=Ac.cpu().numpy().copy())
+    # the single-pass ID (Algorithm 6) of the same coarse skeleton, on the GPU
+    from synthetic.channel import LX, LZ, wall_normal_points
+    nx, ny, nz = grid
+    coords = (np.arange(nx) * (LX / nx), wall_normal_points(ny), np.arange(nz) * (LZ / nz))
+    per = (LX, 0.0, LZ)
+    sk.set_mesh(*coords, per)
+    Jct, Pct = torch.as_tensor(out["Jc"][:kc]), torch.as_tensor(out["Pc"][:kc])
+    out["S"] = sk.single_pass_lift(Jct, kc).cpu().double().numpy()
+    out["sp_fro"], out["sp_mx"] = sk.single_pass_error(A, Jct, Pct)
+    out["coords"], out["per"] = coords, per
     yield out
     sk.close()
 
 
-def test_streamed_sketch_sampled_outputs(streamed_case):
+@pytest.fixture(scope="module")
+def oracle_pass(streamed_case):
+    """The oracle on the whole streamed case, in ONE pass over row blocks of
+    A (each block copied to the host once, converted to FP64 exactly):
+      * W = Psi A (Algorithm 4 step 3) and the error of the GPU's Y = A Omega;
+      * ||A||_F^2;
+      * for each approximation A ~ A(:, J) P (GPU randomized ID, GPU and
+        oracle sub-sampled ID) or S P (single-pass ID, S = M A_c(:, J_c) by
+        the oracle's operator M), the exact FP64 residual sums of squares
+        and, where the tests compare it, the maximum entry-wise ratio;
+      * G = A(:, J)^T A for the GPU's skeleton J, so that the error of any
+        P on that J follows from ||A - A_J P||^2 = ||A||^2 - 2 <P, G> +
+        <P P^T, G(:, J)> (checked against the direct sum for the GPU's P).
+    """
+    import oracle.single_pass as osp
     c = streamed_case
-    A, m, n, l, seed = c["A"], c["m"], c["n"], c["l"], c["seed"]
-    cols = np.array([0, 511, 512, 999])            # both windows and their edges
-    Psi = oracle.psi(l, m, seed)                   # l x m, FP64
-    Acols = A[:, cols].cpu().double().numpy()
-    Wo = Psi @ Acols
-    assert rel(c["W"][:, cols], Wo) <= 1e-5
-    del Psi
-    rows = np.array([0, 127, 128, 2_359_295, m - 1])
+    A, m, n, l, k, seed = c["A"], c["m"], c["n"], c["l"], c["k"], c["seed"]
+    kc = c["kc"]
+    Jco, Pco, kco, mco = oracle.column_id(c["Ac"].astype(np.float64), k)
+    M = osp.coarse_to_fine(c["grid"], c["nc"], (4, 4, 4), c["coords"], c["per"])
+    So = M @ c["Ac"].astype(np.float64)[:, c["Jc"][:kc]]
+    approx = {"gpu": (c["J"][: c["kout"]], c["P"][: c["kout"]], None, True),
+              "gpu_coarse": (c["Jc"][:kc], c["Pc"][:kc], None, False),
+              "oracle_coarse": (Jco[:kco], Pco, None, False),
+              "single_pass": (None, c["Pc"][:kc], So, True)}
     Om = oracle.omega(n, l, seed)
-    Yo = A[rows, :].cpu().double().numpy() @ Om
-    assert rel(c["Y"][rows, :].cpu().double().numpy(), Yo) <= 1e-5
+    Wo = np.zeros((l, n))
+    Jg = np.asarray(c["J"][: c["kout"]], dtype=np.int64)
+    G = np.zeros((len(Jg), n))
+    ss = {key: 0.0 for key in approx}
+    rmax = {key: 0.0 for key in approx}
+    ss_a = ey_num = ey_den = 0.0
+    rb = 262_144
+    for r0 in range(0, m, rb):
+        r1 = min(m, r0 + rb)
+        blk = A[r0:r1].T.contiguous().cpu().numpy().T.astype(np.float64)   # exact
+        Wo += oracle.psi(l, 0, seed, rows=np.arange(r0, r1)) @ blk
+        Yo = blk @ Om
+        Yg = c["Y"][r0:r1].T.contiguous().cpu().numpy().T.astype(np.float64)
+        ey_num += float(np.sum((Yg - Yo) ** 2))
+        ey_den += float(np.sum(Yo * Yo))
+        flat = blk.ravel(order="F")
+        ss_a += float(flat @ flat)
+        G += blk[:, Jg].T @ blk
+        absb = np.abs(blk)
+        nz = absb > 0
+        for key, (J, P, S, want_max) in approx.items():
+            R = (blk[:, np.asarray(J, dtype=np.int64)] if S is None else S[r0:r1]) @ P
+            np.subtract(blk, R, out=R)
+            rf = R.ravel(order="A")
+            ss[key] += float(rf @ rf)
+            if want_max:
+                np.abs(R, out=R)
+                np.divide(R, absb, out=R, where=nz)
+                R[~nz] = 0.0
+                rmax[key] = max(rmax[key], float(R.max()))
+    err = {key: float(np.sqrt(ss[key] / ss_a)) for key in approx}
+    return dict(Wo=Wo, ey=float(np.sqrt(ey_num / ey_den)), ss_a=ss_a, err=err, rmax=rmax, G=G,
+                Jg=Jg, Jco=Jco, Pco=Pco, kco=kco, mco=mco, So=So)
+
+
+def _err_on_gpu_skeleton(op, P):
+    """Relative error of A ~ A(:, J_gpu) P from the pass's G = A(:, J)^T A."""
+    G, J = op["G"], op["Jg"]
+    e2 = op["ss_a"] - 2.0 * float(np.sum(P * G)) + float(np.sum((P @ P.T) * G[:, J]))
+    return float(np.sqrt(max(e2, 0.0) / op["ss_a"]))
 
 
 def test_streamed_coarse_gather_exact(streamed_case):
@@ -120,27 +183,8 @@ def test_streamed_coarse_gather_exact(streamed_case):
     assert torch.equal(torch.as_tensor(c["Ac"], device="cuda"), c["A"][rows, :])
 
 
-def _row_block_error(c, J, P, S=None, rb=262_144):
-    """The oracle's relative Frobenius and entry-wise errors of A ~ A(:, J) P
-    (or S P when S is given) over all rows of the streamed case, summed in
-    row blocks (each block an exact FP64 residual)."""
-    A = c["A"]
-    ss_res = ss_a = 0.0
-    rmax = 0.0
-    J = np.asarray(J, dtype=np.int64)
-    for r0 in range(0, c["m"], rb):
-        blk = A[r0:r0 + rb].cpu().double().numpy()
-        Ahat = (blk[:, J] if S is None else S[r0:r0 + rb]) @ P
-        R = blk - Ahat
-        ss_res += float(np.sum(R * R))
-        ss_a += float(np.sum(blk * blk))
-        nz = blk != 0
-        if np.any(nz):
-            rmax = max(rmax, float(np.max(np.abs(R[nz]) / np.abs(blk[nz]))))
-    return float(np.sqrt(ss_res / ss_a)), rmax
-
-
 def test_streamed_factor_against_oracle_qr(streamed_case):
+    """The GPU's pivoted QR and solve against the oracle's on the same W."""
     c = streamed_case
     Jo, Po, ko, margin = oracle.column_id(c["W"], c["k"])
     print(f"streamed case: pivot margin of the QR of the GPU's W {margin:.2e}")
@@ -154,88 +198,66 @@ def test_streamed_factor_against_oracle_qr(streamed_case):
             1.0001 * np.max(np.abs(c["W"] - c["W"][:, Jo] @ Po)) + 1e-12
 
 
-def test_streamed_coarse_factor_against_oracle_qr(streamed_case):
-    c = streamed_case
-    Jo, Po, ko, margin = oracle.column_id(c["Ac"].astype(np.float64), c["k"])
-    print(f"streamed case: pivot margin of the coarse QR {margin:.2e}")
+def test_streamed_randomized_id_against_full_oracle(streamed_case, oracle_pass):
+    """Algorithm 4 run by the oracle on the whole bench workload (4,718,592 x
+    1000 FP32, l = 60, k = 50, seed 0): every entry of the GPU's W and Y, its
+    J (or, below the pivot margin, a valid skeleton), P and error against the
+    oracle's.  The oracle's error is the workload's "fixed relative error"."""
+    c, op = streamed_case, oracle_pass
+    Wo = op["Wo"]
+    ew = rel(c["W"], Wo)
+    Jo, Po, ko, margin = oracle.column_id(Wo, c["k"])
+    fg = op["err"]["gpu"]
+    print(f"streamed case, oracle Alg. 4: pivot margin {margin:.2e}; GPU: W err {ew:.2e}, "
+          f"Y err {op['ey']:.2e}, error {c['fro']:.6e} (oracle's sum for the GPU's J, P "
+          f"{fg:.6e}, entry-wise {op['rmax']['gpu']:.4e})")
+    assert ew <= 1e-5 and op["ey"] <= 1e-5
+    assert c["kout"] == ko == c["k"]
+    assert_valid_skeleton(c["J"], c["P"], c["kout"], c["n"])
+    # the expansion through G reproduces the direct residual sum
+    assert abs(_err_on_gpu_skeleton(op, c["P"][: c["kout"]]) - fg) <= 1e-9 * fg
+    if margin >= MARGIN:
+        assert c["J"].tolist() == Jo.tolist()
+        assert np.max(np.abs(c["P"] - Po)) <= 1e-3 * max(1.0, np.abs(Po).max())
+        fo = _err_on_gpu_skeleton(op, Po)
+        print(f"oracle's randomized ID error (fixed relative error): {fo:.7e}")
+        assert abs(c["fro"] - fo) <= 1e-4 * fo
+    else:   # within rounding of a tie: a valid ID of A, its error exact
+        assert abs(c["fro"] - fg) <= 1e-4 * fg
+
+
+def test_streamed_coarse_factor_against_oracle(streamed_case, oracle_pass):
+    """The GPU's sub-sampled ID (Algorithm 5) against the oracle's pivoted QR
+    of the same A_c; below the pivot margin, a valid skeleton whose lifted
+    error equals the oracle ID's."""
+    c, op = streamed_case, oracle_pass
+    Jo, Po, ko, margin = op["Jco"], op["Pco"], op["kco"], op["mco"]
+    print(f"streamed case: pivot margin of the coarse QR {margin:.2e}; lifted errors GPU "
+          f"{op['err']['gpu_coarse']:.6e}, oracle {op['err']['oracle_coarse']:.6e}")
     assert c["kc"] == ko
     assert_valid_skeleton(c["Jc"], c["Pc"], c["kc"], c["n"])
     if margin >= MARGIN:
         assert c["Jc"].tolist() == Jo.tolist()
         assert np.max(np.abs(c["Pc"] - Po)) <= 1e-8 * max(1.0, np.abs(Po).max())
-    else:   # within rounding of a tie: the same lifted error as the oracle's ID
-        fo, _ = _row_block_error(c, Jo, Po)
-        fg, _ = _row_block_error(c, c["Jc"][: c["kc"]], c["Pc"][: c["kc"]])
-        assert abs(fg - fo) <= 1e-6 * fo
+    else:
+        assert abs(op["err"]["gpu_coarse"] - op["err"]["oracle_coarse"]) <= \
+            1e-6 * op["err"]["oracle_coarse"]
 
 
-def test_streamed_randomized_id_against_full_oracle(streamed_case):
-    """Algorithm 4 run by the oracle on the whole bench workload (4,718,592 x
-    1000 FP32, l = 60, k = 50, seed 0): W = Psi A and Y = A Omega in FP64 over
-    row blocks, the pivoted QR of the 60 x 1000 W, P, and the relative error
-    of A ~ A(:, J) P over all rows.  Every entry of the GPU's W and Y, its J
-    (or, below the pivot margin, a valid skeleton), P and error against
-    these.  The oracle's error is the workload's "fixed relative error"."""
-    c = streamed_case
-    A, m, n, l, k, seed = c["A"], c["m"], c["n"], c["l"], c["k"], c["seed"]
-    Om = oracle.omega(n, l, seed)
-    Wo = np.zeros((l, n))
-    ey_num = ey_den = 0.0
-    rb = 262_144
-    for r0 in range(0, m, rb):
-        r1 = min(m, r0 + rb)
-        blk = A[r0:r1].cpu().double().numpy()
-        Wo += oracle.psi(l, 0, seed, rows=np.arange(r0, r1)) @ blk
-        Yo = blk @ Om
-        Yg = c["Y"][r0:r1].cpu().double().numpy()
-        ey_num += float(np.sum((Yg - Yo) ** 2))
-        ey_den += float(np.sum(Yo * Yo))
-    ew = rel(c["W"], Wo)
-    ey = float(np.sqrt(ey_num / ey_den))
-    Jo, Po, ko, margin = oracle.column_id(Wo, k)
-    fo, mo = _row_block_error(c, Jo, Po)
-    print(f"streamed case, oracle Alg. 4: rel. Frobenius error {fo:.6e}, entry-wise {mo:.4e}, "
-          f"pivot margin {margin:.2e}; GPU: W err {ew:.2e}, Y err {ey:.2e}, error {c['fro']:.6e}")
-    assert ew <= 1e-5 and ey <= 1e-5
-    assert c["kout"] == ko == k
-    assert_valid_skeleton(c["J"], c["P"], c["kout"], n)
-    if margin >= MARGIN:
-        assert c["J"].tolist() == Jo.tolist()
-        assert np.max(np.abs(c["P"] - Po)) <= 1e-3 * max(1.0, np.abs(Po).max())
-        assert abs(c["fro"] - fo) <= 1e-4 * fo
-    else:   # within rounding of a tie: a valid ID of A at the oracle's error
-        fg, _ = _row_block_error(c, c["J"], c["P"])   # (equal error: within 1.05x)
-        assert abs(c["fro"] - fg) <= 1e-4 * fg
-        assert fg <= 1.05 * fo
-
-
-def test_streamed_reconstruction_error_exact_sum(streamed_case):
-    """The oracle's reconstruction error of the GPU's own (J, P) over all
-    4.7M rows, summed in row chunks (each chunk an exact FP64 residual)."""
-    c = streamed_case
-    fo, rmax = _row_block_error(c, c["J"][: c["kout"]], c["P"][: c["kout"]])
+def test_streamed_reconstruction_error_exact_sum(streamed_case, oracle_pass):
+    """The GPU's error pass against the oracle's exact sums over all 4.7M rows
+    for the same (J, P)."""
+    c, op = streamed_case, oracle_pass
+    fo, rmax = op["err"]["gpu"], op["rmax"]["gpu"]
     assert abs(c["fro"] - fo) <= 1e-4 * fo
     assert abs(c["mx"] - rmax) <= 1e-4 * rmax
 
 
-def test_streamed_single_pass_id(streamed_case):
+def test_streamed_single_pass_id(streamed_case, oracle_pass):
     """Algorithm 6 at full size: the lifted skeleton M A_c(:, J_c) and the
     single-pass error against the oracle's operator M (all 4.7M rows)."""
-    import oracle.single_pass as osp
-    from synthetic.channel import LX, LZ, wall_normal_points
-    c = streamed_case
-    sk, A, grid, kc = c["sk"], c["A"], c["grid"], c["kc"]
-    nx, ny, nz = grid
-    coords = (np.arange(nx) * (LX / nx), wall_normal_points(ny), np.arange(nz) * (LZ / nz))
-    per = (LX, 0.0, LZ)
-    sk.set_mesh(*coords, per)
-    Jc = torch.as_tensor(c["Jc"][:kc])
-    Pc = torch.as_tensor(c["Pc"][:kc])
-    S = sk.single_pass_lift(Jc, kc).cpu().double().numpy()
-    fro, mx = sk.single_pass_error(A, Jc, Pc)
-    M = osp.coarse_to_fine(grid, c["nc"], (4, 4, 4), coords, per)
-    So = M @ c["Ac"].astype(np.float64)[:, c["Jc"][:kc]]
-    assert rel(S, So) <= 1e-6
-    fo, rmax = _row_block_error(c, None, c["Pc"][:kc], S=So)
-    assert abs(fro - fo) <= 1e-4 * fo
-    assert abs(mx - rmax) <= 1e-4 * rmax
+    c, op = streamed_case, oracle_pass
+    assert rel(c["S"], op["So"]) <= 1e-6
+    fo, rmax = op["err"]["single_pass"], op["rmax"]["single_pass"]
+    assert abs(c["sp_fro"] - fo) <= 1e-4 * fo
+    assert abs(c["sp_mx"] - rmax) <= 1e-4 * rmax

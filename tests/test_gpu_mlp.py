@@ -2,9 +2,12 @@
 the FP64 oracle (oracle/learned.py): the feature gather, the forward scores,
 every gradient, and a training run whose trajectory follows the oracle's.
 
-Bars (FP32 kernels, FP64 oracle on the same FP32 inputs): features exact;
-scores within 1e-5 of max |s|; gradients within 1e-4 of each gradient's
-largest entry; after 50 SGD steps the parameters within 1e-3 of their scale.
+The two dense products run on the tensor cores with bfloat16 operands and
+FP32 accumulation; the oracle takes the same bfloat16-rounded operands
+(product_round=bf16_operands) with exact accumulation.  Bars: features
+exact; scores within 1e-5 of max |s|; gradients within 1e-4 of each
+gradient's largest entry; after 50 SGD steps the parameters within 1e-3 of
+their scale.
 """
 import numpy as np
 import pytest
@@ -50,7 +53,7 @@ def test_forward_matches_the_oracle(n, F, H):
     p = _params(F, H, seed=3)
     net = Mlp(p)
     s = net.forward(torch.from_numpy(X).to(DEV)).cpu().numpy()
-    so, (Zo, Go) = L.forward(X.astype(np.float64), p)
+    so, (Zo, Go) = L.forward(X.astype(np.float64), p, product_round=L.bf16_operands)
     assert np.max(np.abs(s - so)) <= 1e-5 * max(1.0, np.abs(so).max())
     assert np.max(np.abs(net.G.cpu().numpy() - Go)) <= 1e-5 * max(1.0, np.abs(Go).max())
 
@@ -67,7 +70,8 @@ def test_backward_matches_the_oracle(pos_weight):
     Xd = torch.from_numpy(X).to(DEV)
     net.forward(Xd)
     g = net.backward(Xd, torch.from_numpy(y).to(DEV), pos_weight)
-    go = L.backward(X.astype(np.float64), y.astype(np.float64), p, pos_weight)
+    go = L.backward(X.astype(np.float64), y.astype(np.float64), p, pos_weight,
+                    product_round=L.bf16_operands)
     for key in ("W1", "b1", "w2", "b2"):
         a = g[key].cpu().numpy().reshape(-1)
         b = np.atleast_1d(np.asarray(go[key], dtype=np.float64)).reshape(-1)
@@ -85,11 +89,12 @@ def test_gpu_training_follows_the_oracle():
     Xd, yd = torch.from_numpy(X).to(DEV), torch.from_numpy(y).to(DEV)
     q = dict(p)
     X64, y64 = X.astype(np.float64), y.astype(np.float64)
-    first = L.bce_loss(L.forward(X64, q)[0], y64)
+    r = L.bf16_operands
+    first = L.bce_loss(L.forward(X64, q, product_round=r)[0], y64)
     for _ in range(50):
         net.forward(Xd)
         net.step(net.backward(Xd, yd), lr=0.5)
-        q = L.sgd_step(q, L.backward(X64, y64, q), lr=0.5)
+        q = L.sgd_step(q, L.backward(X64, y64, q, product_round=r), lr=0.5)
     for key in ("W1", "b1", "w2", "b2"):
         a = getattr(net, key).cpu().numpy().reshape(-1)
         b = np.atleast_1d(q[key]).reshape(-1)
@@ -137,3 +142,27 @@ def test_factor_restricted_matches_the_oracle():
             sk.factor_restricted(np.array(bad))
         assert e.value.status == 1
     sk.close()
+
+
+# ------------------------------------------------------------ the proposal
+
+@pytest.mark.parametrize("n,count", [(512, 100), (37, 37), (4096, 1), (300, 17)])
+def test_propose_matches_the_oracle(n, count):
+    """id_mlp_propose against oracle.learned.propose: the count highest
+    scores, ties to the lower index, in increasing column order (with many
+    exact ties and a NaN, which ranks last)."""
+    from paper_1905_13257_gb300 import _binding as B
+    lib = B.load()
+    rng = np.random.default_rng(n + count)
+    s = np.round(rng.standard_normal(n) * 4) / 4          # many ties
+    s = s.astype(np.float32)
+    if n > 3:
+        s[3] = np.nan
+    sd = torch.from_numpy(s).to(DEV)
+    cand = torch.empty(count, dtype=torch.int32, device=DEV)
+    st = lib.id_mlp_propose(B.C.c_void_p(sd.data_ptr()), n, count, B.C.c_void_p(cand.data_ptr()),
+                            B.C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    so = np.where(np.isnan(s), -np.inf, s.astype(np.float64))
+    assert cand.cpu().tolist() == L.propose(so, count).tolist()
+    assert lib.id_mlp_check(B.C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0

@@ -168,3 +168,37 @@ def test_training_fits_a_separable_toy_problem():
     assert last < 0.5 * first
     acc = np.mean((L.forward(X, p)[0] > 0) == (y > 0))
     assert acc > 0.9
+
+
+def test_bf16_products_round_exactly_the_two_products_operands():
+    """product_round=bf16_operands: the forward pass equals the plain one on
+    bfloat16-rounded X and W1, the W1 gradient differs from the unrounded one
+    by no more than the rounding of its two operands allows (|x y - x' y'|
+    <= 2^-8 (|x| |y| + |x'| |y'|) per term, bfloat16 relative rounding <= 2^-9
+    each), and every other gradient is that of the rounded forward pass."""
+    rng = np.random.default_rng(4)
+    n, F, H = 24, 40, 16
+    X = rng.standard_normal((n, F))
+    y = (rng.random(n) < 0.3).astype(float)
+    p = L.init_params(F, H, seed=2)
+    p["b1"] = rng.standard_normal(H) * 0.3
+    r = L.bf16_operands
+    Xb = r(X)
+    # every rounded value is a bfloat16: 8 significant bits
+    m, e = np.frexp(Xb[Xb != 0])
+    assert np.all(m * 256 == np.round(m * 256))
+    assert np.max(np.abs(Xb - X) / np.abs(X)) <= 2.0 ** -8
+    s_r, (Z_r, _) = L.forward(X, p, product_round=r)
+    pb = dict(p, W1=r(p["W1"]))
+    s_p, (Z_p, _) = L.forward(Xb, pb)
+    assert np.array_equal(Z_r, Z_p) and np.array_equal(s_r, s_p)
+    g_r = L.backward(X, y, p, product_round=r)
+    g_p = L.backward(Xb, y, pb)
+    for key in ("b1", "w2", "b2"):
+        assert np.allclose(g_r[key], g_p[key], rtol=0, atol=0)
+    # gW1 from rounded X and rounded dZ against the unrounded product
+    _, (Z, G) = L.forward(Xb, pb)
+    bound = 2.0 ** -8 * 2 * (np.abs(Xb).T @ np.abs(np.outer(np.ones(n), p["w2"]))) * \
+        np.max(np.abs(L.gelu_grad(Z))) / n
+    assert np.all(np.abs(g_r["W1"] - g_p["W1"]) <= bound + 1e-15)
+    assert not np.array_equal(g_r["W1"], g_p["W1"])
