@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libidsketch.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "sketch_simt.cu", "sketch_tc.cu", "cpqr.cu", "coarse.cu", "recon.cu",
+SOURCES = ["capi.cu", "sketch_simt.cu", "sketch_tc.cu", "cpqr.cu", "coarse.cu", "coarse_coop.cu",
+           "recon.cu",
            "recon_tc.cu", "single_pass.cu", "noalloc.cu", "tma_host.cu", "batch.cu",
            "mlp.cu", "restricted.cu", "gauss_table.cpp"]
 

@@ -7,8 +7,6 @@
 
 #include <vector>
 
-#include <vector>
-
 #include "idsketch.h"
 
 namespace idsk {
@@ -290,6 +288,10 @@ cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double 
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
                            int k, int n, double* P, cudaStream_t st);
 cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
+// The coarse QR as one cooperative launch (coarse_coop.cu): FP32 A_c, m_c a
+// multiple of 4, at most 512 rows per CTA.
+bool coarse_coop_ok(const id_sketch* h);
+cudaError_t launch_coarse_coop(id_sketch* h, int64_t n, cudaStream_t st);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
                                double* out3, int* status, cudaStream_t st,
