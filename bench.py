@@ -104,6 +104,33 @@ def kernel_traffic(kernel_file, kernel_name):
     return None
 
 
+def gpu_numa_cpus(dev_index):
+    """(node, cpus): the host NUMA node sysfs reports for the GPU's PCI device
+    and the CPUs of that node this process may run on; None if unknown."""
+    import subprocess as sp
+    try:
+        out = sp.run(["nvidia-smi", "-i", str(dev_index), "--query-gpu=pci.bus_id",
+                      "--format=csv,noheader"], capture_output=True, text=True, timeout=30)
+        bus = out.stdout.strip().splitlines()[0].strip().lower()
+        parts = bus.split(":")
+        if len(parts) == 3 and len(parts[0]) > 4:   # 00000000:xx:yy.z
+            bus = parts[0][-4:] + ":" + parts[1] + ":" + parts[2]
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for rng in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            if "-" in rng:
+                lo, hi = rng.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif rng:
+                cpus.add(int(rng))
+        cpus &= set(os.sched_getaffinity(0))
+        return (node, cpus) if cpus else None
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -245,7 +272,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sk = IdSketch(m, n, K_RANK, L_SKETCH, seed=SEED, dtype=torch.float32, grid=grid,
                   ncomp=NCOMP, coarse_stride=STRIDE, want_Y=True, want_coarse=True,
-                  window_cols=n, stream=stream)
+                  window_cols=n, stream=stream, prec=args.prec)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
     phase_ms = {"sketch": 0.0, "factor": 0.0, "coarse": 0.0, "recon": 0.0}
@@ -320,11 +347,12 @@ def run_ours(args):
     sketch_bytes = 4.0 * m * n + 4.0 * mc * n + 4.0 * m * L_SKETCH * (2 * launches_per_step - 1)
     ms_s, cnt_s = kt["sketch"]
     sketch_launch_ms = ms_s / max(cnt_s, 1)
-    rl_sketch = {"kernel": "sketch_tc_kernel<2>", "bound": "hbm",
+    kname = "sketch_tc_kernel<2>" if args.prec == "exact" else "sketch_tc_kernel<1>"
+    rl_sketch = {"kernel": kname, "bound": "hbm",
                  "achieved": (sketch_bytes / launches_per_step / (sketch_launch_ms / 1e3) / 1e9
                               if cnt_s else None),
                  "peak": peak, "peak_kind": f"of {peak_kind}", "unit": "GB/s",
-                 "traffic": kernel_traffic("sketch_tc.cu", "sketch_tc_kernel<2>"),
+                 "traffic": kernel_traffic("sketch_tc.cu", kname),
                  "algorithmic_bytes_per_launch": sketch_bytes / launches_per_step,
                  "launch_ms": sketch_launch_ms, "launches_timed": cnt_s,
                  "launches_per_step": launches_per_step,
@@ -350,8 +378,17 @@ def run_ours(args):
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
+        # the pinned host buffer is allocated (and its pages placed) from the
+        # CPUs of the GPU's own NUMA node, so that the copies do not cross
+        # to the other socket's memory
+        numa = gpu_numa_cpus(local)
+        aff = os.sched_getaffinity(0)
+        if numa:
+            os.sched_setaffinity(0, numa[1])
         A_host = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
         A_host.copy_(A.T)
+        if numa:
+            os.sched_setaffinity(0, aff)
         A_host_v = A_host.T
         # Two device buffers: the host-to-device copies of step k + 1 run on a
         # copy stream while step k computes (a stream of snapshot matrices
@@ -409,7 +446,8 @@ def run_ours(args):
         e2e = {"value": world * 4.0 * m * n / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms,
-               "overlap": "host-to-device copies of step k + 1 under the compute of step k"}
+               "overlap": "host-to-device copies of step k + 1 under the compute of step k",
+               "host_numa_node": numa[0] if numa else None}
         del A_host, bufs
 
     cpu = None
@@ -426,8 +464,12 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic channel field (seeded), resident in HBM",
-                "config": cfgd, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+                "dtype": "f32" if args.prec == "exact" else "bf16",
+                "data": "synthetic channel field (seeded), resident in HBM",
+                "config": dict(cfgd, sketch_precision=("FP32-accurate (two bfloat16 pieces)"
+                                                       if args.prec == "exact" else
+                                                       "bfloat16 products, FP32 accumulation")),
+                "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "cpu_baseline": cpu,
                 "errors": {"rel_fro": result.get("fro"), "rel_max": result.get("rel_max"),
                            "k_out": result.get("kout"), "k_coarse": result.get("kc")}}
@@ -662,6 +704,9 @@ def main():
                     default="channel",
                     help="batched64: the batched form (64 matrices of uneven size); "
                          "learned: the learned skeleton proposal (training + comparison)")
+    ap.add_argument("--prec", choices=["exact", "bf16"], default="exact",
+                    help="sketch precision of the channel workload: FP32-accurate (default) "
+                         "or the bfloat16 precision form")
     ap.add_argument("--train-windows", type=int, default=200)
     ap.add_argument("--held-windows", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=4)

@@ -75,16 +75,19 @@ def cpqr(B, k, rank_tol_factor=RANK_TOL_FACTOR):
              largest residual norms; pivot parity is only meaningful when it is
              comfortably above rounding level
     """
-    M = np.array(B, dtype=np.float64, copy=True)
+    from scipy.linalg.blas import dger
+    M = np.array(B, dtype=np.float64, order="F", copy=True)   # columns contiguous
     rows, n = M.shape
     kmax = min(int(k), rows, n)
     pivoted = np.zeros(n, dtype=bool)
     J = []
     R = np.zeros((kmax, n))
-    tol = rank_tol_factor * EPS64 * np.sqrt(float(np.sum(M * M)))
+    tol = rank_tol_factor * EPS64 * np.sqrt(float(np.einsum("ij,ij->", M, M)))
     margin = np.inf
+    vfull = np.zeros(rows)
     for s in range(kmax):
-        nu = np.sqrt(np.sum(M[s:, :] * M[s:, :], axis=0))
+        Ms = M[s:, :]
+        nu = np.sqrt(np.einsum("ij,ij->j", Ms, Ms))   # ||B^(s)(s:, j)||, afresh
         nu[pivoted] = -1.0
         p = int(np.argmax(nu))          # first maximum = lowest index
         if not nu[p] > tol:
@@ -95,9 +98,15 @@ def cpqr(B, k, rank_tol_factor=RANK_TOL_FACTOR):
         v, tau, beta = householder(M[s:, p])
         pivoted[p] = True
         J.append(p)
-        others = ~pivoted
-        if tau != 0.0 and np.any(others):
-            M[s:, others] -= tau * np.outer(v, v @ M[s:, others])
+        if tau != 0.0:
+            # H = I - tau v v^T on rows s.. of the non-pivoted columns: the
+            # rank-one update B(s:, j) -= tau v (v^T B(s:, j)) (BLAS dger on
+            # the whole matrix, v zero above row s; pivoted columns get w = 0)
+            w = v @ Ms
+            w[pivoted] = 0.0
+            vfull[:] = 0.0
+            vfull[s:] = v
+            M = dger(-tau, vfull, w, a=M, overwrite_a=True)
         M[s, p] = beta
         M[s + 1:, p] = 0.0
         R[s, :] = M[s, :]

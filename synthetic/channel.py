@@ -31,7 +31,11 @@ Field
 Structure: the clean field is exactly S T with S (m x 128) and T (128 x n),
 so its rank is at most 128.  ``gap_k`` keeps the gap_k/2 largest modes at full
 amplitude and scales the others by 1e-3, which makes a clear gap after the
-gap_k-th singular value (inputs on which the skeleton is unambiguous).
+gap_k-th singular value, and gives every mode a slow amplitude envelope
+1 + 0.5 sin(2 pi (h_mode + t / t_window)) over the window (still two rows of
+T per mode): on a periodic grid the snapshots of a pure travelling wave all
+have the same norm, which would make the first pivot of a deterministic ID a
+tie; with the envelope the skeleton is unambiguous.
 
 Layout: row r = ((c*ny + j)*nz + kz)*nx + i (component slowest, then y, then
 z, x fastest); A is column-major (each snapshot contiguous), returned as a
@@ -124,8 +128,11 @@ def factors(grid, ncomp, n, seed, gap_k=None, device="cpu", first=0, dt=None):
             S[c * plane:(c + 1) * plane, 2 * mi + 1] = sn
         h = (0.618034 * (mi + 1)) % 1.0
         om = ax * U_C * (0.75 + 0.5 * h)
-        T[2 * mi] = torch.cos(om * t)
-        T[2 * mi + 1] = torch.sin(om * t)
+        env = 1.0
+        if gap_k is not None:   # slow amplitude envelope: snapshot norms differ
+            env = 1.0 + 0.5 * torch.sin(2.0 * math.pi * (h + t / (step * max(n, 1))))
+        T[2 * mi] = env * torch.cos(om * t)
+        T[2 * mi + 1] = env * torch.sin(om * t)
     # unit RMS: ||S T||_F^2 = trace((S^T S)(T T^T))
     fro2 = torch.sum((S.T @ S) * (T @ T.T)).item()
     S *= 1.0 / math.sqrt(fro2 / (m * max(n, 1)))

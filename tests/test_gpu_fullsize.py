@@ -105,7 +105,17 @@ def streamed_case():
     out["S"] = sk.single_pass_lift(Jct, kc).cpu().double().numpy()
     out["sp_fro"], out["sp_mx"] = sk.single_pass_error(A, Jct, Pct)
     out["coords"], out["per"] = coords, per
+    # the precision form (BF16 sketch products) on the same data
+    skb = _sk(m=m, n_max=n, k=k, l=l, seed=seed, dtype=torch.float32, prec="bf16", want_Y=True,
+              window_cols=n)
+    for j0 in range(0, n, 32):
+        skb.stream_columns(A[:, j0:j0 + 32])
+    Jb, Pb, kb = skb.factor()
+    Wb, Yb, _ = skb.sketches()
+    out["bf16"] = dict(J=Jb.cpu().numpy(), P=Pb.cpu().numpy(), kout=kb, W=Wb.cpu().numpy().copy(),
+                       Y=Yb, fro=skb.reconstruct_error(A, Jb[:kb], Pb[:kb])[0], sk=skb)
     yield out
+    skb.close()
     sk.close()
 
 
@@ -130,7 +140,9 @@ def oracle_pass(streamed_case):
     Jco, Pco, kco, mco = oracle.column_id(c["Ac"].astype(np.float64), k)
     M = osp.coarse_to_fine(c["grid"], c["nc"], (4, 4, 4), c["coords"], c["per"])
     So = M @ c["Ac"].astype(np.float64)[:, c["Jc"][:kc]]
+    cb = c["bf16"]
     approx = {"gpu": (c["J"][: c["kout"]], c["P"][: c["kout"]], None, True),
+              "bf16": (cb["J"][: cb["kout"]], cb["P"][: cb["kout"]], None, False),
               "gpu_coarse": (c["Jc"][:kc], c["Pc"][:kc], None, False),
               "oracle_coarse": (Jco[:kco], Pco, None, False),
               "single_pass": (None, c["Pc"][:kc], So, True)}
@@ -140,7 +152,7 @@ def oracle_pass(streamed_case):
     G = np.zeros((len(Jg), n))
     ss = {key: 0.0 for key in approx}
     rmax = {key: 0.0 for key in approx}
-    ss_a = ey_num = ey_den = 0.0
+    ss_a = ey_num = ey_den = eyb_num = 0.0
     rb = 262_144
     for r0 in range(0, m, rb):
         r1 = min(m, r0 + rb)
@@ -150,6 +162,8 @@ def oracle_pass(streamed_case):
         Yg = c["Y"][r0:r1].T.contiguous().cpu().numpy().T.astype(np.float64)
         ey_num += float(np.sum((Yg - Yo) ** 2))
         ey_den += float(np.sum(Yo * Yo))
+        Yb = cb["Y"][r0:r1].T.contiguous().cpu().numpy().T.astype(np.float64)
+        eyb_num += float(np.sum((Yb - Yo) ** 2))
         flat = blk.ravel(order="F")
         ss_a += float(flat @ flat)
         G += blk[:, Jg].T @ blk
@@ -167,7 +181,8 @@ def oracle_pass(streamed_case):
                 rmax[key] = max(rmax[key], float(R.max()))
     err = {key: float(np.sqrt(ss[key] / ss_a)) for key in approx}
     return dict(Wo=Wo, ey=float(np.sqrt(ey_num / ey_den)), ss_a=ss_a, err=err, rmax=rmax, G=G,
-                Jg=Jg, Jco=Jco, Pco=Pco, kco=kco, mco=mco, So=So)
+                Jg=Jg, Jco=Jco, Pco=Pco, kco=kco, mco=mco, So=So,
+                ey_bf16=float(np.sqrt(eyb_num / ey_den)))
 
 
 def _err_on_gpu_skeleton(op, P):
@@ -261,3 +276,29 @@ def test_streamed_single_pass_id(streamed_case, oracle_pass):
     fo, rmax = op["err"]["single_pass"], op["rmax"]["single_pass"]
     assert abs(c["sp_fro"] - fo) <= 1e-4 * fo
     assert abs(c["sp_mx"] - rmax) <= 1e-4 * rmax
+
+
+def test_streamed_bf16_precision_form_against_full_oracle(streamed_case, oracle_pass):
+    """The precision form (sketch products with A rounded to bfloat16, FP32
+    accumulation; QR and solve in FP64) against the FP64 oracle of the FP32
+    data, at the bench workload.  Bars derived from the rounding: a bfloat16
+    keeps 8 significant bits, so each entry of A moves by at most 2^-9 of its
+    value and the sketches by at most about that in relative Frobenius norm;
+    the ID it picks must reconstruct A within 1.05x the oracle's error (the
+    equal-error bar).  The J overlap and every error are printed."""
+    c, op = streamed_case, oracle_pass
+    cb = c["bf16"]
+    Jo, Po, ko, margin = oracle.column_id(op["Wo"], c["k"])
+    ew = rel(cb["W"], op["Wo"])
+    fo = _err_on_gpu_skeleton(op, Po) if c["J"].tolist() == Jo.tolist() else op["err"]["gpu"]
+    fb = op["err"]["bf16"]
+    overlap = len(set(cb["J"][: cb["kout"]].tolist()) & set(Jo.tolist())) / ko
+    Pdiff = float(np.max(np.abs(cb["P"] - Po))) if cb["J"].tolist() == Jo.tolist() else None
+    print(f"BF16 form vs FP64 oracle: W {ew:.3e}, Y {op['ey_bf16']:.3e}, J overlap {overlap:.2f}, "
+          f"max|P - P_o| {Pdiff}, error {fb:.6e} (oracle {fo:.6e}, ratio {fb / fo:.5f}; "
+          f"GPU's own error pass {cb['fro']:.6e})")
+    assert ew <= 2.0 ** -9 and op["ey_bf16"] <= 2.0 ** -9
+    assert cb["kout"] == c["k"]
+    assert_valid_skeleton(cb["J"], cb["P"], cb["kout"], c["n"])
+    assert fb <= 1.05 * fo
+    assert abs(cb["fro"] - fb) <= 1e-4 * fb
