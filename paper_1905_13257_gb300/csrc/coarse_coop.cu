@@ -59,6 +59,20 @@ constexpr int CI_P = 0, CI_STOP = 1, CI_NREC = 2, CI_KOUT = 3, CI_BAR_CNT = 4, C
 __device__ __forceinline__ int nrec_slot(int s) { return (s & 1) ? CI_NREC_ODD : CI_NREC; }
 constexpr int CS_ALPHA = 0, CS_SIGMA = 1, CS_BETA = 2, CS_TAU = 3, CS_DEN = 4, CS_TOL = 5;
 
+// Optional timeline of CTA 0 (clock64 at the phase boundaries of every step),
+// compiled only when IDSK_CC_TRACE is defined by a profiling harness.
+#ifdef IDSK_CC_TRACE
+__device__ long long g_cc_trace[64 * 16];
+#define CC_TRACE(s, point)                                                        \
+  do {                                                                            \
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (s) < 64) g_cc_trace[(s) * 16 + (point)] = clock64(); \
+  } while (0)
+#else
+#define CC_TRACE(s, point) \
+  do {                     \
+  } while (0)
+#endif
+
 struct CoopArgs {
   const float* Ac;
   int64_t mc;
@@ -345,6 +359,7 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
   for (; ok && s < a.kmax; ++s) {
     // ---------------------------------------------------------- phase A
     // pivot: largest residual norm, ties to the lowest index
+    CC_TRACE(s, 0);
     {
       unsigned long long v = 0ull;
       int idx = 0x7fffffff;
@@ -398,6 +413,7 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
       cons_sync();
     }
     if (stop_now) break;
+    CC_TRACE(s, 1);
     const int p = piv;
     for (int t = tid; t < s; t += CT) fp[t] = df_of(a.F[(int64_t)t * a.ldf + p]);
     const double sig_prev = scal[1], den_prev = scal[4];
@@ -440,13 +456,25 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
     }
     for (int rr = nrows + tid; rr < 4 * QMAX; rr += CT) uhs[rr] = uls[rr] = 0.f;
     cons_sync();
-    // partials of V_s^T u (warp w: t = w, w + 16, ...) and ||u||^2
+    CC_TRACE(s, 2);
+    // partials of V_s^T u (warp w: t = w, w + 16, ...) and ||u||^2; every
+    // load of a lane's rows is in flight before the sums (rows lane + 32 e)
     for (int t = warp; t < s; t += CW) {
       float hh = 0.f, hl = 0.f;
       const float2* vc = a.V + (int64_t)t * mc + r0;
-      for (int rr = lane; rr < nrows; rr += 32) {
-        const float2 pr = df_mul(vc[rr], make_float2(uhs[rr], uls[rr]));
-        df_add(hh, hl, pr.x, pr.y);
+      float2 vv[QMAX * 4 / 32];
+#pragma unroll
+      for (int e = 0; e < QMAX * 4 / 32; ++e) {
+        const int rr = lane + 32 * e;
+        vv[e] = rr < nrows ? vc[rr] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int e = 0; e < QMAX * 4 / 32; ++e) {
+        const int rr = lane + 32 * e;
+        if (rr < nrows) {
+          const float2 pr = df_mul(vv[e], make_float2(uhs[rr], uls[rr]));
+          df_add(hh, hl, pr.x, pr.y);
+        }
       }
       warp_pair_sum(hh, hl);
       if (lane == 0) a.upart[(int64_t)b * HP + t] = df_norm(hh, hl);
@@ -462,21 +490,28 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
       }
       a.upart[(int64_t)b * HP + kLMax] = df_norm(acc.x, acc.y);
     }
+    CC_TRACE(s, 3);
     if (!grid_sync(a, &sflag)) {
       ok = false;
       break;
     }
     // ---------------------------------------------------------- phase B
+    CC_TRACE(s, 4);
     // Householder scalars and h = V_s^T v_s, every CTA from the partials in
     // CTA order (quantity q: warp q % CW, lanes stride the CTAs, then a
     // fixed shuffle tree)
     for (int q = warp; q <= kLMax; q += CW) {
       if (q >= s && q != kLMax) continue;
       float ah = 0.f, al = 0.f;
-      for (int bb = lane; bb < G; bb += 32) {
-        const float2 x = a.upart[(int64_t)bb * HP + q];
-        df_add(ah, al, x.x, x.y);
+      float2 xv[8];   // G <= 256: every CTA partial of the lane in flight
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int bb = lane + 32 * e;
+        xv[e] = bb < G ? a.upart[(int64_t)bb * HP + q] : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (lane + 32 * e < G) df_add(ah, al, xv[e].x, xv[e].y);
       warp_pair_sum(ah, al);
       if (lane == 0) hs[q] = (double)ah + (double)al;
     }
@@ -515,7 +550,9 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
       }
     }
     // A^T u over this CTA's rows (u is zero at and above row s)
+    CC_TRACE(s, 5);
     ok = cons_all(pass(1));
+    CC_TRACE(s, 6);
     if (!ok && tid == 0) atomicOr(a.status, 1);
     if (!grid_sync(a, &sflag) || !ok) {
       ok = false;
@@ -523,16 +560,32 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
     }
     // ---------------------------------------------------------- phase C
     // the CTA's columns: warp w takes c0 + w, c0 + w + 16, ...
+    CC_TRACE(s, 7);
     {
       const double tau = scal[3], den = scal[4], sigma = scal[1];
       for (int j = c0 + warp; j < c1; j += CW) {
+        double gv[8], fv[2];   // every load of the lane in flight (G <= 256, s <= 64)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int bb = lane + 32 * e;
+          gv[e] = bb < G ? a.gpart[(int64_t)bb * n + j] : 0.0;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int t = lane + 32 * e;
+          fv[e] = t < s ? a.F[(int64_t)t * a.ldf + j] : 0.0;
+        }
         double gs = 0.0;
-        for (int bb = lane; bb < G; bb += 32) gs += a.gpart[(int64_t)bb * n + j];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) gs += gv[e];
         double fh = 0.0, rr = 0.0;
-        for (int t = lane; t < s; t += 32) {
-          const double f = a.F[(int64_t)t * a.ldf + j];
-          fh += f * hvec[t];
-          rr += vrow[t] * f;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int t = lane + 32 * e;
+          if (t < s) {
+            fh += fv[e] * hvec[t];
+            rr += vrow[t] * fv[e];
+          }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -561,10 +614,12 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
         }
       }
     }
+    CC_TRACE(s, 8);
     if (!grid_sync(a, &sflag)) {
       ok = false;
       break;
     }
+    CC_TRACE(s, 9);
     // norms that lost too many bits: recomputed from their definition
     // ||A^(s+1)(s+1:, j)||^2 in FP64, rows split over the CTAs
     if (tid == 0) nrec_s = *(volatile int*)&a.cint[nrec_slot(s)];
@@ -618,6 +673,16 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
 
 }  // namespace
 
+#ifdef IDSK_CC_TRACE
+// Profiling harness only: clock64 of CTA 0 at the phase boundaries, entry
+// [s * 16 + point]: 0 step start, 1 pivot chosen, 2 u formed, 3 partials
+// written, 4 after barrier 1, 5 scalars done, 6 pass over A_c done, 7 after
+// barrier 2, 8 columns finalized, 9 after barrier 3.
+extern "C" int idsk_cc_trace_read(long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, g_cc_trace, sizeof(g_cc_trace));
+}
+#endif
+
 // Whether the cooperative form serves this handle: FP32 A_c with m_c a
 // multiple of 4 (16-byte row quads) and at most 512 rows per CTA.
 bool coarse_coop_ok(const id_sketch* h) {
@@ -630,7 +695,7 @@ bool coarse_coop_ok(const id_sketch* h) {
   }
   const int64_t Q = h->mc / 4;
   const int64_t G = std::min<int64_t>(h->nsm, Q);
-  return Q >= 1 && (Q + G - 1) / G <= QMAX && h->coarse_blocks >= G;
+  return Q >= 1 && G <= 256 && (Q + G - 1) / G <= QMAX && h->coarse_blocks >= G;
 }
 
 cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {

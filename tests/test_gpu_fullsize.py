@@ -170,7 +170,8 @@ def oracle_pass(streamed_case):
         absb = np.abs(blk)
         nz = absb > 0
         for key, (J, P, S, want_max) in approx.items():
-            R = (blk[:, np.asarray(J, dtype=np.int64)] if S is None else S[r0:r1]) @ P
+            Ab = blk[:, np.asarray(J, dtype=np.int64)] if S is None else S[r0:r1]
+            R = (P.T @ Ab.T).T          # A_hat of the block, column-major like blk
             np.subtract(blk, R, out=R)
             rf = R.ravel(order="A")
             ss[key] += float(rf @ rf)
