@@ -599,6 +599,7 @@ def run_learned(args):
     stride = (grid[0] // 16, grid[1] // 16, grid[2] // 16)
     sk = IdSketch(m, nwin, K_RANK, L_SKETCH, seed=SEED, dtype=torch.float32, want_Y=False)
     prop = LearnedProposal(grid, K_RANK, stride=stride, seed=1)
+    untrained = LearnedProposal(grid, K_RANK, stride=stride, seed=1)
     t0 = time.perf_counter()
     data = []
     for w in range(ntrain):
@@ -620,10 +621,11 @@ def run_learned(args):
         losses.append(tot / len(data))
     prop.net.check()
     t_train = time.perf_counter() - t0
+    untrained.scale = prop.scale
     rng = np.random.default_rng(7)
     rows = []
     for w in range(ntrain, ntrain + nheld):
-        rows.append(compare_on_window(prop, sk, window(w), rng))
+        rows.append(compare_on_window(prop, sk, window(w), rng, untrained=untrained))
     # one window's ID, each form: stream (sketch) + QR (+ proposal) + error pass
     A = window(ntrain)
     X = prop.features(A)
@@ -658,6 +660,7 @@ def run_learned(args):
     wbytes = 4.0 * m * nwin
     ratio_l = [r["err_learned"] / r["err_plain"] for r in rows]
     ratio_r = [r["err_random"] / r["err_plain"] for r in rows]
+    ratio_u = [r["err_untrained"] / r["err_plain"] for r in rows]
     line = {
         "metric": "learned skeleton proposal vs plain randomized ID at equal error (<= 1.05x)",
         "value": wbytes / (times["learned"] / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
@@ -666,13 +669,16 @@ def run_learned(args):
         "data": "synthetic channel-field stream (seeded), windows of 512 snapshots",
         "config": {"workload": f"learned proposal: {ntrain} training + {nheld} held-out windows "
                                f"of {grid[0]}x{grid[1]}x{grid[2]}x{NCOMP} = {m} rows x {nwin} "
-                               f"snapshots FP32, k={K_RANK}, l={L_SKETCH}, 2k candidates, "
+                               f"snapshots FP32, k={K_RANK}, l={L_SKETCH}, 2 candidates in each "
+                               f"of k ranges of snapshots, "
                                f"4096 features, 256 hidden units, BF16 products",
                    "epochs": args.epochs, "lr": args.lr},
         "plain_ms_per_window": times["plain"],
         "plain_GBs": wbytes / (times["plain"] / 1e3) / 1e9,
         "training": {"loss_per_epoch": losses, "data_s": t_data, "train_s": t_train},
         "held_out": {"err_ratio_learned": ratio_l, "err_ratio_random": ratio_r,
+                     "err_ratio_untrained": ratio_u,
+                     "recall_untrained": float(np.mean([r["recall_untrained"] for r in rows])),
                      "proposal_used": int(sum(r["use_learned"] for r in rows)),
                      "windows": len(rows),
                      "recall_learned": float(np.mean([r["recall_learned"] for r in rows])),

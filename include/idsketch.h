@@ -346,6 +346,16 @@ id_status id_mlp_sgd(float* d_p, const float* d_g, int64_t count, float lr, void
 id_status id_mlp_propose(const float* d_s, int64_t n, int32_t count, int32_t* d_cand,
                          void* cuda_stream);
 
+/* The stratified proposal: the n columns form `strata` consecutive ranges
+ * [q n / strata, (q + 1) n / strata) (snapshots in time order) and each range
+ * gives its `per` columns of highest score (ties to the lower index, NaN
+ * last).  The candidates go to d_cand (device int32, room for strata * per) in
+ * increasing column order and their number (strata * per, or fewer when a
+ * range holds fewer than per columns) to d_ncand (device int32, may be NULL).
+ * 1 <= strata <= n <= 4096, per >= 1. */
+id_status id_mlp_propose_stratified(const float* d_s, int64_t n, int32_t strata, int32_t per,
+                                    int32_t* d_cand, int32_t* d_ncand, void* cuda_stream);
+
 /* Synchronises cuda_stream and reports whether a bounded device wait of the
  * tensor-core products gave up since the last check (ID_ERR_TIMEOUT; the
  * affected outputs hold NaN, the flag is cleared) or ID_OK. */

@@ -22,7 +22,9 @@ here:
 * training target: y_j = 1 when column j is in the skeleton the plain
   randomized ID picked on that window, else 0; loss: the mean binary cross
   entropy of sigmoid(s) against y, positives optionally weighted;
-* proposal: the 2k columns of highest score (ties to the lower index); the
+* proposal: the 2k columns of highest score (ties to the lower index), or,
+  stratified, the 2 highest in each of k consecutive ranges of snapshots (the
+  skeleton of a window spreads over its time span); the
   pivoted QR of W restricted to them gives J, and P over all columns is the
   least-squares fit of W on W(:, J), which for a pivoted QR equals
   R11^-1 R12 (Sec. 2.4), with P(:, J) = I exactly;
@@ -174,6 +176,19 @@ def propose(scores, count):
     scores = np.asarray(scores, dtype=np.float64)
     order = np.lexsort((np.arange(len(scores)), -scores))
     return np.sort(order[:count])
+
+
+def propose_stratified(scores, strata, per):
+    """The per highest scores (ties to the lower index) in each of strata
+    consecutive column ranges [floor(q n / strata), floor((q + 1) n / strata)),
+    all sorted: candidates spread over the window's snapshots in time."""
+    scores = np.asarray(scores, dtype=np.float64)
+    n = len(scores)
+    out = []
+    for q in range(strata):
+        lo, hi = (q * n) // strata, ((q + 1) * n) // strata
+        out.extend((lo + propose(scores[lo:hi], min(per, hi - lo))).tolist())
+    return np.sort(np.array(out, dtype=np.int64))
 
 
 def restricted_id(B, cand, k):

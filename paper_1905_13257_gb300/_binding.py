@@ -109,6 +109,8 @@ SIGNATURES = {
     "id_mlp_sgd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p]),
     "id_mlp_check": (C.c_int, [C.c_void_p]),
     "id_mlp_propose": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "id_mlp_propose_stratified": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "id_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "id_timing_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                  C.POINTER(C.c_int64)]),

@@ -934,7 +934,10 @@ cudaError_t run(id_sketch* h, int64_t n64, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st) {
-  if (coarse_coop_ok(h)) return launch_coarse_coop(h, n, st);
+  if (coarse_coop_ok(h)) {
+    const cudaError_t e = launch_coarse_coop(h, n, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (h->cfg.dtype == ID_F64) return run<double>(h, n, st);
   return run<float>(h, n, st);
 }

@@ -32,6 +32,7 @@
 // its own bulk copies before it exits.
 #include <float.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -93,7 +94,7 @@ struct CoopArgs {
   int* status;
   int keep_cols;        // columns whose ring loads are kept in L2 (evict_last)
   int sgc;              // columns per ring stage
-  uint32_t seg;         // bytes per column segment in a stage (rows_max * 4)
+  int box_rows;         // rows per TMA box (two boxes cover a CTA's rows)
   double tol_factor;
 };
 
@@ -177,7 +178,8 @@ __device__ __forceinline__ void warp_pair_sum(float& h, float& l) {
   }
 }
 
-__global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
+__global__ void __launch_bounds__(NTH, 1)
+    coarse_coop_kernel(CoopArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * RING];
   __shared__ int abort_flag, stop_flag, sflag;
@@ -206,9 +208,10 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
   const int nq = (int)(q1 - q0);
   const int c0 = (int)((int64_t)n * b / G), c1 = (int)((int64_t)n * (b + 1) / G);
   const int sgc = a.sgc;
-  const uint32_t seg = a.seg;
+  const int box_rows = a.box_rows;
+  const uint32_t box_bytes = (uint32_t)(box_rows * sgc * 4);
   const int nstage = (n + sgc - 1) / sgc;
-  const uint32_t stage_bytes = (uint32_t)sgc * seg;
+  const uint32_t stage_bytes = 2u * box_bytes;
 
   if (tid == 0) {
     for (int q = 0; q < RING; ++q) {
@@ -225,9 +228,12 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
   if (warp == CW) {
     // ------------------------------------------------------------ producer
     // Stage u holds columns [sgc * (u % nstage), ...) of this CTA's rows, for
-    // pass u / nstage (pass 0: the norms, pass 1 + s: step s).  A_c does not
-    // change, so the producer runs ahead across steps, bounded by the ring.
+    // pass u / nstage (pass 0: the norms, pass 1 + s: step s), as two TMA
+    // boxes of box_rows rows x sgc columns (column-major, zero fill past the
+    // matrix).  A_c does not change, so the producer runs ahead across steps,
+    // bounded by the ring.
     if (lane == 0) {
+      const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
       const uint64_t keep = tc::policy_evict_last(), stream = tc::policy_evict_first();
       const int64_t total = (int64_t)(1 + a.kmax) * nstage;
       int64_t u = 0;
@@ -252,12 +258,12 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
         }
         const int st = (int)(u % nstage);
         const int j0 = st * sgc;
-        const int ncols = min(sgc, n - j0);
-        tc::mbar_expect_tx(full0 + 8u * slot, (uint32_t)(ncols * nrows * 4));
-        for (int c = 0; c < ncols; ++c)
-          tc::bulk_g2s_hint(ring + (uint32_t)slot * stage_bytes + (uint32_t)c * seg,
-                            a.Ac + (int64_t)(j0 + c) * mc + r0, (uint32_t)(nrows * 4),
-                            full0 + 8u * slot, j0 + c < a.keep_cols ? keep : stream);
+        const uint64_t pol = j0 < a.keep_cols ? keep : stream;
+        tc::mbar_expect_tx(full0 + 8u * slot, stage_bytes);
+        tc::tma_load_2d(ring + (uint32_t)slot * stage_bytes, tm, (int)r0, j0, full0 + 8u * slot,
+                        pol);
+        tc::tma_load_2d(ring + (uint32_t)slot * stage_bytes + box_bytes, tm, (int)r0 + box_rows,
+                        j0, full0 + 8u * slot, pol);
       }
       // every issued copy has landed before the CTA exits (bounded)
       const int64_t issued = u;
@@ -295,13 +301,16 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
       const int j0 = st * sgc;
       const int ncols = min(sgc, n - j0);
       for (int c = warp; c < ncols; c += CW) {
-        const uint8_t* col = ringp + (size_t)slot * stage_bytes + (size_t)c * seg;
+        // row quad q of column c: box 0 (rows < box_rows) or box 1
+        const uint8_t* col0 = ringp + (size_t)slot * stage_bytes + (size_t)c * box_rows * 4;
+        const uint8_t* col1 = col0 + box_bytes - (size_t)box_rows * 4;
         float hi = 0.f, lo = 0.f;
 #pragma unroll
         for (int e = 0; e < QMAX / 32; ++e) {
           const int q = lane + 32 * e;
           if (q < nq) {
-            const float4 x = *reinterpret_cast<const float4*>(col + 16 * q);
+            const float4 x = *reinterpret_cast<const float4*>(
+                4 * q < box_rows ? col0 + 16 * q : col1 + 16 * q);
             if (mode == 0) {
               df_acc(hi, lo, x.x, x.x, 0.f);
               df_acc(hi, lo, x.y, x.y, 0.f);
@@ -500,20 +509,31 @@ __global__ void __launch_bounds__(NTH, 1) coarse_coop_kernel(CoopArgs a) {
     // Householder scalars and h = V_s^T v_s, every CTA from the partials in
     // CTA order (quantity q: warp q % CW, lanes stride the CTAs, then a
     // fixed shuffle tree)
-    for (int q = warp; q <= kLMax; q += CW) {
-      if (q >= s && q != kLMax) continue;
-      float ah = 0.f, al = 0.f;
-      float2 xv[8];   // G <= 256: every CTA partial of the lane in flight
+    // (two quantities per round, every CTA partial of the lane in flight)
+    for (int q0 = warp; q0 <= kLMax; q0 += 2 * CW) {
+      int qq[2] = {q0, q0 + CW};
+      bool use[2];
+      float2 xv[2][8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int bb = lane + 32 * e;
-        xv[e] = bb < G ? a.upart[(int64_t)bb * HP + q] : make_float2(0.f, 0.f);
+      for (int h = 0; h < 2; ++h) {
+        use[h] = qq[h] <= kLMax && (qq[h] < s || qq[h] == kLMax);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int bb = lane + 32 * e;
+          xv[h][e] = (use[h] && bb < G) ? a.upart[(int64_t)bb * HP + qq[h]]
+                                        : make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (lane + 32 * e < G) df_add(ah, al, xv[e].x, xv[e].y);
-      warp_pair_sum(ah, al);
-      if (lane == 0) hs[q] = (double)ah + (double)al;
+      for (int h = 0; h < 2; ++h) {
+        if (!use[h]) continue;
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (lane + 32 * e < G) df_add(ah, al, xv[h][e].x, xv[h][e].y);
+        warp_pair_sum(ah, al);
+        if (lane == 0) hs[qq[h]] = (double)ah + (double)al;
+      }
     }
     cons_sync();
     if (tid == 0) {
@@ -723,8 +743,12 @@ cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
   a.cint = h->d_cint;
   a.cscal = h->d_cscal;
   a.status = h->d_status;
-  a.seg = (uint32_t)(qmax * 16);
-  a.sgc = (int)std::max<int64_t>(1, std::min<int64_t>(16, STAGE_MAX / a.seg));
+  a.box_rows = (int)(4 * ((qmax + 1) / 2));   // two boxes of at most 256 rows
+  a.sgc = (int)std::max<int64_t>(1, std::min<int64_t>(16, STAGE_MAX / (8 * a.box_rows)));
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  if (!make_tmap_f32_2d(h->d_Ac, h->mc, n, h->mc, a.box_rows, a.sgc, &tm))
+    return cudaErrorNotSupported;   // the multi-launch path serves it
   a.tol_factor = ID_RANK_TOL_FACTOR;
   int l2 = 0;
   if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev) != cudaSuccess) {
@@ -733,12 +757,12 @@ cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
   }
   // about 3/8 of L2 holds the leading columns of A_c from one step to the next
   a.keep_cols = (int)std::min<int64_t>(n, (int64_t)(0.375 * l2 / (4.0 * (double)h->mc)));
-  const size_t smem = 128 + (size_t)RING * a.sgc * a.seg;
+  const size_t smem = 128 + (size_t)RING * 8 * a.box_rows * a.sgc;
   cudaError_t e = cudaFuncSetAttribute(coarse_coop_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(h->d_cint, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
-  void* args[] = {&a};
+  void* args[] = {&a, &tm};
   e = cudaLaunchCooperativeKernel((const void*)coarse_coop_kernel, dim3(G), dim3(NTH), args,
                                   smem, st);
   if (e != cudaSuccess) return e;

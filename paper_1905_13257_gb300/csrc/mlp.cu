@@ -293,8 +293,13 @@ __device__ __forceinline__ int score_key(float v) {
   return b >= 0 ? b : (int)(0x80000000u - (unsigned)b) - 1;   // monotone in v
 }
 
+// strata > 1: the columns form `strata` consecutive ranges [q n / strata,
+// (q + 1) n / strata) and column j competes only within its range for `count`
+// places (the stratified proposal); strata = 1: one range.
 __global__ void __launch_bounds__(PR_THREADS) propose_kernel(const float* __restrict__ s, int n,
-                                                              int count, int* __restrict__ cand) {
+                                                              int count, int strata,
+                                                              int* __restrict__ cand,
+                                                              int* __restrict__ ncand) {
   __shared__ int key[PR_MAX];
   __shared__ unsigned char take[PR_MAX];
   __shared__ int wsum[PR_THREADS / 32];
@@ -302,8 +307,13 @@ __global__ void __launch_bounds__(PR_THREADS) propose_kernel(const float* __rest
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += PR_THREADS) {
     const int kj = key[j];
+    // the range holding j: the largest q with q n / strata <= j
+    int q = (int)(((int64_t)j * strata) / n);
+    while (q + 1 < strata && ((int64_t)(q + 1) * n) / strata <= j) ++q;
+    while (q > 0 && ((int64_t)q * n) / strata > j) --q;
+    const int lo = (int)(((int64_t)q * n) / strata), hi = (int)(((int64_t)(q + 1) * n) / strata);
     int above = 0;
-    for (int i = 0; i < n; ++i) above += (key[i] > kj) || (key[i] == kj && i < j);
+    for (int i = lo; i < hi; ++i) above += (key[i] > kj) || (key[i] == kj && i < j);
     take[j] = above < count;
   }
   __syncthreads();
@@ -330,6 +340,7 @@ __global__ void __launch_bounds__(PR_THREADS) propose_kernel(const float* __rest
     base += tot;
     __syncthreads();
   }
+  if (threadIdx.x == 0 && ncand) *ncand = base;
 }
 
 id_status cuda_status(cudaError_t e) {
@@ -416,7 +427,18 @@ id_status id_mlp_propose(const float* d_s, int64_t n, int32_t count, int32_t* d_
                          void* cuda_stream) {
   if (!d_s || !d_cand || n < 1 || n > PR_MAX || count < 1 || count > n)
     return ID_ERR_INVALID_ARG;
-  propose_kernel<<<1, PR_THREADS, 0, (cudaStream_t)cuda_stream>>>(d_s, (int)n, count, d_cand);
+  propose_kernel<<<1, PR_THREADS, 0, (cudaStream_t)cuda_stream>>>(d_s, (int)n, count, 1, d_cand,
+                                                                   nullptr);
+  count_launches(1);
+  return cuda_status(cudaGetLastError());
+}
+
+id_status id_mlp_propose_stratified(const float* d_s, int64_t n, int32_t strata, int32_t per,
+                                    int32_t* d_cand, int32_t* d_ncand, void* cuda_stream) {
+  if (!d_s || !d_cand || n < 1 || n > PR_MAX || strata < 1 || strata > n || per < 1)
+    return ID_ERR_INVALID_ARG;
+  propose_kernel<<<1, PR_THREADS, 0, (cudaStream_t)cuda_stream>>>(d_s, (int)n, per, strata,
+                                                                   d_cand, d_ncand);
   count_launches(1);
   return cuda_status(cudaGetLastError());
 }

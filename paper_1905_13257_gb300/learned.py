@@ -75,16 +75,32 @@ class LearnedProposal:
         self.net.step(self.net.backward(X, y, pos_weight), lr)
         return s
 
-    def propose(self, X, count=None):
-        """The count (default 2k) columns of highest score, increasing order
-        (a CUDA int32 tensor)."""
-        count = 2 * self.k if count is None else int(count)
-        s = self.net.forward(X)
-        cand = torch.empty(count, dtype=torch.int32, device=X.device)
-        B.check(self.lib.id_mlp_propose(B.C.c_void_p(s.data_ptr()), s.numel(), count,
-                                        B.C.c_void_p(cand.data_ptr()), self.net._sh),
-                "id_mlp_propose")
-        return cand
+    def propose(self, X, count=None, stratified=True):
+        """2k candidate columns (a CUDA int32 tensor, increasing order): by
+        default the 2 highest scores in each of k consecutive ranges of the
+        window's snapshots (id_mlp_propose_stratified); stratified=False takes
+        the count (default 2k) highest scores overall (id_mlp_propose)."""
+        return propose_from_scores(self.lib, self.net.forward(X), self.k, count, stratified,
+                                   self.net._sh)
+
+
+def propose_from_scores(lib, s, k, count=None, stratified=True, sh=None):
+    """Candidates from scores s (CUDA FP32) by the library's proposal kernels."""
+    sh = B.C.c_void_p(torch.cuda.current_stream().cuda_stream) if sh is None else sh
+    n = s.numel()
+    if stratified:
+        cand = torch.empty(2 * k, dtype=torch.int32, device=s.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=s.device)
+        B.check(lib.id_mlp_propose_stratified(B.C.c_void_p(s.data_ptr()), n, k, 2,
+                                              B.C.c_void_p(cand.data_ptr()),
+                                              B.C.c_void_p(cnt.data_ptr()), sh),
+                "id_mlp_propose_stratified")
+        return cand[: int(cnt.item())]
+    count = 2 * k if count is None else int(count)
+    cand = torch.empty(count, dtype=torch.int32, device=s.device)
+    B.check(lib.id_mlp_propose(B.C.c_void_p(s.data_ptr()), n, count,
+                               B.C.c_void_p(cand.data_ptr()), sh), "id_mlp_propose")
+    return cand
 
 
 def bce(s, y, pos_weight):
@@ -105,38 +121,42 @@ def plain_skeleton(sk, A, chunk=32):
     return J[:kout], P[:kout]
 
 
-def compare_on_window(prop, sk, A, rng, count=None, timer=None):
-    """Plain randomized ID against the learned proposal (and random
-    candidates) on one window: errors, fallback decision, candidate recall and
-    the time of the pivoted QR over n columns against the restricted one."""
+def compare_on_window(prop, sk, A, rng, untrained=None):
+    """Plain randomized ID against the learned proposal on one window (and
+    against the same proposal rule fed by an untrained network and by random
+    scores): reconstruction errors, the fallback decision (proposal used when
+    its error is within 1.05x the plain one's), recall of the plain skeleton
+    by the candidates, and the time of the pivoted QR over all n columns
+    against scoring + proposal + the QR restricted to the candidates."""
     k = prop.k
     n = A.shape[1]
-    count = 2 * k if count is None else count
     sk.reset()
     for j0 in range(0, n, 32):
         sk.stream_columns(A[:, j0:j0 + 32])
     sk.flush()
+    X = prop.features(A)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Jp, Pp, kp = sk.factor()
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    X = prop.features(A)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    cand = prop.propose(X, count)
+    cand = prop.propose(X)
     Jl, Pl, kl = sk.factor_restricted(cand)
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
-    rand = torch.as_tensor(np.sort(rng.choice(n, count, replace=False)), dtype=torch.int32,
-                           device="cuda")
-    Jr, Pr, kr = sk.factor_restricted(rand)
+    jp = set(Jp[:kp].cpu().tolist())
     ep, _ = sk.reconstruct_error(A, Jp[:kp], Pp[:kp])
     el, _ = sk.reconstruct_error(A, Jl[:kl], Pl[:kl])
-    er, _ = sk.reconstruct_error(A, Jr[:kr], Pr[:kr])
-    jp = set(Jp[:kp].cpu().tolist())
-    return {"err_plain": ep, "err_learned": el, "err_random": er,
-            "use_learned": el <= 1.05 * ep,
-            "recall_learned": len(jp & set(cand.cpu().tolist())) / max(kp, 1),
-            "recall_random": len(jp & set(rand.cpu().tolist())) / max(kp, 1),
-            "qr_plain_s": t_plain, "proposal_and_qr_s": t_learned}
+    out = {"err_plain": ep, "err_learned": el, "use_learned": el <= 1.05 * ep,
+           "recall_learned": len(jp & set(cand.cpu().tolist())) / max(kp, 1),
+           "qr_plain_s": t_plain, "proposal_and_qr_s": t_learned}
+    others = {"random": torch.as_tensor(rng.random(n), dtype=torch.float32, device="cuda")}
+    if untrained is not None:
+        others["untrained"] = untrained.net.forward(X)
+    for name, sc in others.items():
+        c = propose_from_scores(prop.lib, sc, k)
+        Jo, Po, ko = sk.factor_restricted(c)
+        out[f"err_{name}"] = sk.reconstruct_error(A, Jo[:ko], Po[:ko])[0]
+        out[f"recall_{name}"] = len(jp & set(c.cpu().tolist())) / max(kp, 1)
+    return out

@@ -166,3 +166,21 @@ def test_propose_matches_the_oracle(n, count):
     so = np.where(np.isnan(s), -np.inf, s.astype(np.float64))
     assert cand.cpu().tolist() == L.propose(so, count).tolist()
     assert lib.id_mlp_check(B.C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+
+
+@pytest.mark.parametrize("n,strata,per", [(512, 50, 2), (100, 7, 2), (9, 3, 3), (4096, 64, 1)])
+def test_propose_stratified_matches_the_oracle(n, strata, per):
+    from paper_1905_13257_gb300 import _binding as B
+    lib = B.load()
+    rng = np.random.default_rng(n + strata)
+    s = (np.round(rng.standard_normal(n) * 4) / 4).astype(np.float32)
+    sd = torch.from_numpy(s).to(DEV)
+    cand = torch.full((strata * per,), -7, dtype=torch.int32, device=DEV)
+    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    sh = B.C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.id_mlp_propose_stratified(B.C.c_void_p(sd.data_ptr()), n, strata, per,
+                                         B.C.c_void_p(cand.data_ptr()),
+                                         B.C.c_void_p(cnt.data_ptr()), sh) == 0
+    want = L.propose_stratified(s.astype(np.float64), strata, per)
+    assert int(cnt.item()) == len(want)
+    assert cand[: len(want)].cpu().tolist() == want.tolist()

@@ -202,3 +202,21 @@ def test_bf16_products_round_exactly_the_two_products_operands():
         np.max(np.abs(L.gelu_grad(Z))) / n
     assert np.all(np.abs(g_r["W1"] - g_p["W1"]) <= bound + 1e-15)
     assert not np.array_equal(g_r["W1"], g_p["W1"])
+
+
+def test_propose_stratified_by_brute_force():
+    """Each stratum contributes its `per` best columns (ties to the lower
+    index), checked by sorting each stratum by hand; one stratum reduces to
+    propose()."""
+    rng = np.random.default_rng(3)
+    for n, strata, per in [(100, 7, 2), (512, 50, 2), (9, 3, 3), (50, 50, 1)]:
+        sc = np.round(rng.standard_normal(n) * 3) / 3     # ties
+        got = L.propose_stratified(sc, strata, per)
+        want = []
+        for q in range(strata):
+            lo, hi = q * n // strata, (q + 1) * n // strata
+            idx = sorted(range(lo, hi), key=lambda j: (-sc[j], j))[:per]
+            want += idx
+        assert got.tolist() == sorted(want)
+    sc = rng.standard_normal(40)
+    assert L.propose_stratified(sc, 1, 8).tolist() == L.propose(sc, 8).tolist()
