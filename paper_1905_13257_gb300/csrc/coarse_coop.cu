@@ -8,22 +8,20 @@
 // range of columns for the per-column updates.  Per step s, with pivot p:
 //   A  pivot from the norms (every CTA, same data, same choice); scale
 //      column s-1 of V into v_{s-1}; for the CTA's rows
-//        u = A(:, p) - V_s F(p, :)^T     (rows >= s; kept as column s of V)
-//      and the CTA's partials of V_s^T u and ||u||^2 (rows > s);
+//        u = A(:, p) - V_s F(p, :)^T     (rows >= s; kept as column s of V),
+//      the CTA's partials of V_s^T u and ||u||^2 (rows > s), and its share
+//      of A^T u: its rows of every column, streamed from HBM in TMA boxes
+//      through a shared-memory ring (the producer warp runs ahead across
+//      steps: A_c does not change), one partial per (CTA, column);
 //   -- grid barrier --
 //   B  every CTA sums the partials (in CTA order) into the Householder
 //      scalars alpha = u_s, beta, tau, den = alpha - beta and h = V_s^T v_s;
-//      then its share of A^T u: its rows of every column, streamed from HBM
-//      by bulk copies into a shared-memory ring (the producer warp runs
-//      ahead across steps: A_c does not change), one partial per (CTA,
-//      column);
-//   -- grid barrier --
 //   C  for the CTA's columns: g_j = A(s, j) + (A^T u)_j / den, F(j, s),
 //      R(s, j) and the norm downdate (a norm that lost more than 20 bits is
 //      recomputed from its definition, rows split over the CTAs);
 //   -- grid barrier --
 // A^T v_s = A(s, :)^T + (A^T u below row s) / (u_s - beta) lets the pass over
-// A_c start before the scalars exist.  The arithmetic is that of the
+// A_c run before the scalars exist, so a step needs two grid barriers.  The arithmetic is that of the
 // multi-launch path in coarse.cu: the passes over rows in FP32 pairs (about
 // 48 bits), scalars, F, R and the norms in FP64, every sum in a fixed order.
 //
@@ -500,40 +498,43 @@ __global__ void __launch_bounds__(NTH, 1)
       a.upart[(int64_t)b * HP + kLMax] = df_norm(acc.x, acc.y);
     }
     CC_TRACE(s, 3);
-    if (!grid_sync(a, &sflag)) {
+    // A^T u over this CTA's rows (u is zero at and above row s): it needs
+    // only this CTA's u, so it runs before the barrier
+    ok = cons_all(pass(1));
+    CC_TRACE(s, 4);
+    if (!ok && tid == 0) atomicOr(a.status, 1);
+    if (!grid_sync(a, &sflag) || !ok) {
       ok = false;
       break;
     }
     // ---------------------------------------------------------- phase B
-    CC_TRACE(s, 4);
+    CC_TRACE(s, 5);
     // Householder scalars and h = V_s^T v_s, every CTA from the partials in
-    // CTA order (quantity q: warp q % CW, lanes stride the CTAs, then a
-    // fixed shuffle tree)
-    // (two quantities per round, every CTA partial of the lane in flight)
-    for (int q0 = warp; q0 <= kLMax; q0 += 2 * CW) {
-      int qq[2] = {q0, q0 + CW};
-      bool use[2];
-      float2 xv[2][8];
+    // a fixed order: quantity g (V_t^T u for g = t < s, ||u||^2 for g = s) is
+    // summed by the 8 threads 8 g .. 8 g + 7, thread j over the CTAs b = j
+    // mod 8 (all its loads in flight), then a 3-level shuffle tree
+    {
+      const int g = tid >> 3, j = tid & 7;
+      const int q = g < s ? g : (g == s ? kLMax : -1);
+      float ah = 0.f, al = 0.f;
+      for (int e0 = 0; e0 < (256 + 7) / 8; e0 += 16) {   // 16 loads in flight
+        float2 xv[16];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        use[h] = qq[h] <= kLMax && (qq[h] < s || qq[h] == kLMax);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int bb = lane + 32 * e;
-          xv[h][e] = (use[h] && bb < G) ? a.upart[(int64_t)bb * HP + qq[h]]
-                                        : make_float2(0.f, 0.f);
+        for (int e = 0; e < 16; ++e) {
+          const int bb = j + 8 * (e0 + e);
+          xv[e] = (q >= 0 && bb < G) ? a.upart[(int64_t)bb * HP + q] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (j + 8 * (e0 + e) < G) df_add(ah, al, xv[e].x, xv[e].y);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!use[h]) continue;
-        float ah = 0.f, al = 0.f;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (lane + 32 * e < G) df_add(ah, al, xv[h][e].x, xv[h][e].y);
-        warp_pair_sum(ah, al);
-        if (lane == 0) hs[qq[h]] = (double)ah + (double)al;
+      for (int o = 1; o < 8; o <<= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, ah, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, al, o);
+        df_add(ah, al, oh, ol);
       }
+      if (j == 0 && q >= 0) hs[q] = (double)ah + (double)al;
     }
     cons_sync();
     if (tid == 0) {
@@ -569,18 +570,10 @@ __global__ void __launch_bounds__(NTH, 1)
         vrow[t] = vst;
       }
     }
-    // A^T u over this CTA's rows (u is zero at and above row s)
-    CC_TRACE(s, 5);
-    ok = cons_all(pass(1));
-    CC_TRACE(s, 6);
-    if (!ok && tid == 0) atomicOr(a.status, 1);
-    if (!grid_sync(a, &sflag) || !ok) {
-      ok = false;
-      break;
-    }
+    cons_sync();
     // ---------------------------------------------------------- phase C
     // the CTA's columns: warp w takes c0 + w, c0 + w + 16, ...
-    CC_TRACE(s, 7);
+    CC_TRACE(s, 6);
     {
       const double tau = scal[3], den = scal[4], sigma = scal[1];
       for (int j = c0 + warp; j < c1; j += CW) {
@@ -634,12 +627,12 @@ __global__ void __launch_bounds__(NTH, 1)
         }
       }
     }
-    CC_TRACE(s, 8);
+    CC_TRACE(s, 7);
     if (!grid_sync(a, &sflag)) {
       ok = false;
       break;
     }
-    CC_TRACE(s, 9);
+    CC_TRACE(s, 8);
     // norms that lost too many bits: recomputed from their definition
     // ||A^(s+1)(s+1:, j)||^2 in FP64, rows split over the CTAs
     if (tid == 0) nrec_s = *(volatile int*)&a.cint[nrec_slot(s)];
@@ -696,8 +689,8 @@ __global__ void __launch_bounds__(NTH, 1)
 #ifdef IDSK_CC_TRACE
 // Profiling harness only: clock64 of CTA 0 at the phase boundaries, entry
 // [s * 16 + point]: 0 step start, 1 pivot chosen, 2 u formed, 3 partials
-// written, 4 after barrier 1, 5 scalars done, 6 pass over A_c done, 7 after
-// barrier 2, 8 columns finalized, 9 after barrier 3.
+// written, 4 pass over A_c done, 5 after the first barrier, 6 scalars done,
+// 7 columns finalized, 8 after the second barrier.
 extern "C" int idsk_cc_trace_read(long long* host) {
   return (int)cudaMemcpyFromSymbol(host, g_cc_trace, sizeof(g_cc_trace));
 }

@@ -473,6 +473,18 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     uint32_t wpar = 0, wseen = 0;   // per W^T tile: flush-count parity, flushed before
     for (int i = 0; i < nloc; ++i) {
       const int pb = i & 1;
+      // a later window adds into Y: its old values of row block i + 2 are
+      // prefetched into L2 now (the warp's 32 rows of every sketch column),
+      // so that the read-modify-write at the drain waits for L2, not HBM
+      // (a bulk prefetch needs 16-byte aligned addresses: m a multiple of 4)
+      if (a.want_Y && a.y_accumulate && (a.m & 3) == 0 && i + 2 < nloc) {
+        const int64_t r2 = (rb_begin + i + 2) * TR + q * 32;
+        if (r2 + 32 <= a.m)
+          for (int j = lane; j < a.l; j += 32)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 128;" ::"l"(
+                             reinterpret_cast<const float*>(a.Y) + r2 + (int64_t)j * a.m)
+                         : "memory");
+      }
       // flushes due after this row block first: each W^T tile's barrier is
       // committed right after that tile's MMAs, and the next row block's
       // MMAs wait for the tile to be read out
