@@ -303,12 +303,10 @@ cudaError_t launch_recon_tc(const float* A, int64_t lda, int64_t m, int64_t n, c
                             const InterpGeom* interp = nullptr);
 void build_axis_weights(const double* x, int n, int stride, double period, AxisW* out);
 // Tensor map of an FP32 column-major matrix (rows contiguous, leading
-// dimension ld), boxes of box_rows x box_cols, zero fill outside; with
-// swizzle128 (box_rows = 32: one 128-byte line per column) the 16-byte
-// chunk q of box line c lands at chunk q ^ (c & 7).  False when it cannot be
-// built (alignment, no driver entry point).
+// dimension ld), boxes of box_rows x box_cols, zero fill outside; false when
+// it cannot be built (alignment, no driver entry point).
 bool make_tmap_f32_2d(const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                      int box_cols, CUtensorMap* tm, bool swizzle128 = false);
+                      int box_cols, CUtensorMap* tm);
 cudaError_t launch_skeleton_compact(const void* Ac, int64_t mc, int dtype, const int* Jc, int k,
                                     void* Sc, cudaStream_t st);
 cudaError_t launch_single_pass_lift(const InterpGeom& g, int64_t m, int dtype, int k, void* S,

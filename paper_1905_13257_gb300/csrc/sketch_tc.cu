@@ -16,24 +16,18 @@
 // are added (round to nearest) into a per-CTA FP32 slab, about 30 partials
 // per entry, and the slabs are summed in FP64.
 //
-// Operand layout.  A piece tile is stored in 128-byte-swizzled 1 KB atoms of
-// 8 columns x 64 rows (rows contiguous).  Read as K-major it is the A operand
-// of the W^T product (M = columns, K = rows); read as MN-major it is the A
-// operand of the Y product (M = rows, K = columns).  The TMA form keeps a
-// second copy of each piece in TMEM (lane = column, rows packed two per
-// 32-bit column) and feeds the W^T product's A operand from there: the
-// shared-memory port then carries only the Y product's A reads and the B
-// operands (about 2.4K instead of 2.9K wavefronts per 128 x 128 tile), and
-// the converters and the MMAs contend less for it.  Psi(:, R)^T and
-// Omega(C, :)^T are K-major B operands.
+// Shared-memory layout.  A piece tile is stored in 128-byte-swizzled 1 KB
+// atoms of 8 columns x 64 rows (rows contiguous).  Read as K-major it is the
+// A operand of the W^T product (M = columns, K = rows); read as MN-major it is
+// the A operand of the Y product (M = rows, K = columns): one copy serves both
+// products.  Psi(:, R)^T and Omega(C, :)^T are K-major B operands.
 //
 // Warp roles (one CTA per SM, persistent over a contiguous range of row
 // blocks):
-//   warps 0-7    converters: split A into the pieces and gather coarse rows;
-//                TMA form: from 128-byte-swizzled boxes in a shared-memory
-//                ring, one column per thread, into the swizzled piece slots
-//                and the TMEM piece regions; register form: 128-bit loads in
-//                half tiles into double-buffered piece buffers
+//   warps 0-7    converters: load A with 128-bit coalesced loads in half
+//                tiles (three register buffers: two half tiles in flight),
+//                split into pieces, store them to the swizzled piece buffer
+//                (double-buffered), gather coarse rows
 //   warps 8-11   epilogue: draw Psi for upcoming row blocks (counter
 //                generator), drain Y to global memory, flush W^T partials
 //                into a per-CTA FP32 slab in L2 (one 128-column tile at a
@@ -79,7 +73,6 @@ constexpr int TMEM_COLS = 512;
 constexpr uint32_t IDESC_W = tc::idesc_bf16(128, LP, 0);   // A^T K-major (K = rows)
 constexpr uint32_t IDESC_Y = tc::idesc_bf16(128, LP, 1);   // A MN-major (M = rows)
 constexpr int TMEM_Y = kTcMaxTiles * LP;             // Y accumulators after W^T
-constexpr int TMEM_A = TMEM_Y + 2 * LP;               // TMA form: W^T A operand, 2 slots
 
 // Optional timeline of CTA 0 (clock64 stamps per role), compiled only when
 // IDSK_TC_TRACE is defined by a profiling harness.
@@ -151,23 +144,6 @@ __device__ __noinline__ void gather_column(const float* col, const int64_t* rcs,
       const int64_t rcv = rcs[rr];
       if (rcv >= 0) Ac[rcv] = col[rr];
     }
-}
-
-// Coarse rows of one column held in two swizzled TMA boxes (this thread's 64
-// rows; box line `line`, row r of the 64 at box r / 32, chunk (r % 32) / 4
-// ^ (line & 7)): rows whose coarse index is set go to A_c.  Out of line for
-// the instruction cache, as gather_column.
-__device__ __noinline__ void gather_column_sw(const uint8_t* box, const int64_t* rcs, int line,
-                                              float* Ac) {
-#pragma unroll 1
-  for (int r = 0; r < 64; ++r) {
-    const int64_t rcv = rcs[r];
-    if (rcv >= 0) {
-      const int rl = r & 31;
-      Ac[rcv] = *reinterpret_cast<const float*>(box + (r >> 5) * 4096 +
-                                                ((((rl >> 2) ^ (line & 7))) << 4) + (rl & 3) * 4);
-    }
-  }
 }
 
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
@@ -248,10 +224,10 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       mbar_init(bar(B_WE0 + ct), NEPI);
     }
     mbar_init(bar(B_DONE), 1);
-    if (TMA) {   // stage j of a tile is read by converter warps j and j + 4
+    if (TMA) {
       for (int st = 0; st < NST; ++st) {
         mbar_init(bar(B_RF0 + st), 1);
-        mbar_init(bar(B_RE0 + st), 2);
+        mbar_init(bar(B_RE0 + st), NCONV);
       }
     }
     st_volatile_shared(S.abort_flag, 0);
@@ -290,19 +266,15 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   if (warp < NCONV) {
     if constexpr (TMA) {
     // ------------------------------------------------------ converters (TMA)
-    // The tile's columns arrive as four stages of 32 columns x 128 rows, each
-    // four TMA boxes of 32 rows x 32 columns with the 128-byte swizzle (box
-    // line = one column's 32 rows, 16-byte chunk q at chunk q ^ (column &
-    // 7)).  Warps j and j + 4 take stage j: thread (lane L) owns column
-    // 32 j + L, warp j rows 0-63, warp j + 4 rows 64-127.  Each thread reads
-    // its rows four at a time (conflict-free through the swizzle) and writes
-    //   * the swizzled shared-memory piece (the MN-major A operand of the Y
-    //     product), 8 bytes per row quad;
-    //   * its TMEM lane (lane = column, the A operand of the W^T product, rows
-    //     packed two per 32-bit column), 32 columns per piece with tcgen05.st.
-    const int j = warp & 3, h = warp >> 2;
-    const int cc = 32 * j + lane;                   // column inside the tile
-    const uint32_t t_lane = (uint32_t)(32 * j) << 16;
+    // Raw FP32 boxes (32 columns x 128 rows, 512 B per column) arrive in an
+    // NST-stage ring; thread (warp w, lane l) splits one column, rows
+    // 4(l%8) + 32g of each box into the (single) piece buffer.  The eight
+    // lanes of a quarter warp share a column; the two quarters of each half
+    // warp take columns 4 apart, so that every 8-byte store phase covers all
+    // 32 banks of the 128-byte-swizzled piece (columns c and c + 4 have
+    // disjoint 16-byte chunk positions for rows 0-31).
+    const int cl = (warp >> 1) * 8 + (warp & 1) * 2 + ((lane >> 3) & 1) * 4 + (lane >> 4);
+    const int rq = (lane & 7) * 4;
     int64_t* rcs = reinterpret_cast<int64_t*>(smem_raw + (S.rc - smem_u32(smem_raw)));
     const uint8_t* rawp = smem_raw + (S.raw - smem_u32(smem_raw));
     int t = 0;
@@ -321,50 +293,51 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         gather = conv_bar_or(rcv >= 0);
       }
       for (int ct = 0; ct < nct && ok; ++ct, ++t) {
-        // Piece units u = NP t + p take the two slots in turn (slot u & 1:
-        // shared-memory piece and TMEM region): with NP = 2 the MMAs of one
-        // piece run while the converters write the other.
+        // Piece units u = NP t + p take the two piece slots in turn (slot
+        // u & 1, its (u >> 1)-th use): with NP = 2 the MMAs of one piece run
+        // while the converters write the other.
         const int u0 = NP * t, s0 = u0 & 1;
         if ((u0 >> 1) >= 1 &&
             !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag)) {
           ok = false;
           break;
         }
-        tc_fence_after();
         if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t);
-        const int st = (4 * t + j) % NST;
-        if (!mbar_wait(bar(B_RF0 + st), ((4 * t + j) / NST) & 1, S.abort_flag)) {
-          ok = false;
-          break;
-        }
-        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 1);
-        const uint8_t* box = rawp + st * RAW_BYTES + (2 * h) * 4096 + lane * 128;
         const uint32_t hi_buf = S.pieces + (uint32_t)s0 * PIECE_BYTES;
-        uint32_t hw[32], lw[32];
+        uint32_t lo_keep[NP > 1 ? 32 : 1];   // second piece, packed, until its slot frees
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {   // rows 64 h + 4 q .. + 3
-          const float4 x = *reinterpret_cast<const float4*>(
-              box + (q >> 3) * 4096 + ((((q & 7) ^ (lane & 7))) << 4));
-          const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
-          hw[2 * q] = h01;
-          hw[2 * q + 1] = h23;
-          st_shared_v2(hi_buf + swz((uint32_t)cc, (uint32_t)(64 * h + 4 * q), 2048u), h01, h23);
-          if (NP > 1) {
-            const float2 f01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h01));
-            const float2 f23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h23));
-            lw[2 * q] = pack_bf16x2(x.x - f01.x, x.y - f01.y);
-            lw[2 * q + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
+        for (int j = 0; j < 4; ++j) {
+          const int u = 4 * t + j, st = u % NST;
+          if (ok && !mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) ok = false;
+          if (!ok) continue;
+          if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 1 + j);
+          const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
+          const int cc = 32 * j + cl;              // column inside the tile
+          const int wc = ct * TCOLS + cc;          // column inside the window
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int rr = 32 * g + rq;
+            const float4 x = *reinterpret_cast<const float4*>(raw + cl * TR + rr);
+            const uint32_t off = swz((uint32_t)cc, (uint32_t)rr, 2048u);
+            const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
+            st_shared_v2(hi_buf + off, h01, h23);
+            if (NP > 1) {
+              const float2 f01 =
+                  __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h01));
+              const float2 f23 =
+                  __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h23));
+              lo_keep[(j * 4 + g) * 2] = pack_bf16x2(x.x - f01.x, x.y - f01.y);
+              lo_keep[(j * 4 + g) * 2 + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
+            }
           }
+          if (gather && wc < w.ncols)
+            gather_column(raw + cl * TR, rcs, rq,
+                          reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc));
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_RE0 + st));
         }
-        const int wc = ct * TCOLS + cc;          // column inside the window
-        if (gather && wc < w.ncols)
-          gather_column_sw(box, rcs + 64 * h, lane,
-                           reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc));
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_RE0 + st));
-        tmem_st32(tmem + t_lane + (uint32_t)(TMEM_A + 64 * s0 + 32 * h), hw);
+        if (!ok) break;
         fence_proxy_async();
-        tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_FULL0 + s0));
         if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 5);
@@ -375,15 +348,15 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             ok = false;
             break;
           }
-          tc_fence_after();
           if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 6);
 #pragma unroll
-          for (int q = 0; q < 16; ++q)
-            st_shared_v2(S.pieces + PIECE_BYTES + swz((uint32_t)cc, (uint32_t)(64 * h + 4 * q), 2048u),
-                         lw[2 * q], lw[2 * q + 1]);
-          tmem_st32(tmem + t_lane + (uint32_t)(TMEM_A + 64 + 32 * h), lw);
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+              st_shared_v2(S.pieces + PIECE_BYTES +
+                               swz((uint32_t)(32 * j + cl), (uint32_t)(32 * g + rq), 2048u),
+                           lo_keep[(j * 4 + g) * 2], lo_keep[(j * 4 + g) * 2 + 1]);
           fence_proxy_async();
-          tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_FULL1));
         }
@@ -640,12 +613,8 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           for (int kk = 0; kk < 8; ++kk) {   // W^T: K = 16 rows per instruction
             const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
             const uint32_t acc = ((accw >> ct) & 1u) | (uint32_t)(p | kk);
-            if (TMA)   // A^T from TMEM: 8 columns (16 rows) per instruction
-              mma_bf16_ta(wtm, tmem + (uint32_t)(TMEM_A + 64 * (u & 1) + 8 * kk),
-                          sdesc(psi_s + ko, 0u, 2048u), IDESC_W, acc);
-            else
-              mma_bf16(wtm, sdesc(pa + ko, 0u, 2048u), sdesc(psi_s + ko, 0u, 2048u), IDESC_W,
-                       acc);
+            mma_bf16(wtm, sdesc(pa + ko, 0u, 2048u), sdesc(psi_s + ko, 0u, 2048u), IDESC_W,
+                     acc);
           }
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {   // Y: K = 16 columns per instruction
@@ -696,12 +665,9 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           break;
         }
         TC_TRACE(3, u);
-        // stage = 32 columns x 128 rows as four swizzled boxes of 32 x 32
         mbar_expect_tx(bar(B_RF0 + st), RAW_BYTES);
-#pragma unroll
-        for (int sb = 0; sb < 4; ++sb)
-          tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES + 4096u * sb, tm, row + 32 * sb,
-                      ct * TCOLS + 32 * j, bar(B_RF0 + st), stream_once);
+        tma_load_2d(S.raw + (uint32_t)st * RAW_BYTES, tm, row, ct * TCOLS + 32 * j,
+                    bar(B_RF0 + st), stream_once);
       }
     }
   }
@@ -745,8 +711,7 @@ bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
   if (w.nseg != 1) return false;
   const char* env = getenv("IDSKETCH_SKETCH_TMA");
   if (env && env[0] == '0') return false;
-  return make_tmap_f32_2d(w.seg[0].ptr, a.m, w.seg[0].ncols, w.seg[0].ld, 32, 32, tm,
-                          /*swizzle128=*/true);
+  return make_tmap_f32_2d(w.seg[0].ptr, a.m, w.seg[0].ncols, w.seg[0].ld, TR, 32, tm);
 }
 
 template <int NP, bool TMA>
@@ -769,9 +734,8 @@ cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int d
 
 #ifdef IDSK_TC_TRACE
 // Profiling harness only: the clock64 timeline of CTA 0 ([4][8192]): role 0
-// converter warp 0 (per tile t: 8t first slot free, 8t+1 its stage in, 8t+5
-// first piece out, 8t+6 second slot free, 8t+7 second piece out; register
-// form: t per tile), role 1 MMA (2u piece
+// converter warp 0 (per tile t: 8t start, 8t+1+j box j in, 8t+5 first piece
+// out, 8t+6 second slot free, 8t+7 second piece out), role 1 MMA (2u piece
 // unit u ready, 2u+1 issued), role 2 epilogue (per row block i: 4i flushes
 // done, 4i+1 Y ready, 4i+2 Y drained, 4i+3 Psi drawn), role 3 producer (box u
 // issued).

@@ -32,8 +32,7 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 bool make_tmap_f32_2d(const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                      int box_cols, CUtensorMap* tm, bool swizzle128) {
-  if (swizzle128 && box_rows * 4 != 128) return false;   // one 128-byte line per column
+                      int box_cols, CUtensorMap* tm) {
   if ((((uintptr_t)ptr) & 15u) != 0 || (ld & 3) != 0 || rows < 1 || cols < 1) return false;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -42,8 +41,7 @@ bool make_tmap_f32_2d(const void* ptr, int64_t rows, int64_t cols, int64_t ld, i
   const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
   const cuuint32_t es[2] = {1u, 1u};
   return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
-             es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
