@@ -76,9 +76,6 @@ __device__ long long g_rc_trace[4][4096];
   } while (0)
 #endif
 
-// piece products: (A piece, P piece)
-__constant__ int kCombA[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int kCombP[6] = {0, 1, 0, 2, 1, 0};
 
 template <typename T>
 struct Kahan {
@@ -368,14 +365,19 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       RC_TRACE(2, i);
       const uint32_t sb = s_s + (uint32_t)sbuf * 3u * S_PIECE;
       const uint32_t d = tmem + (uint32_t)(b * TN);
+      // base descriptors of the three pieces of each operand; a K step only
+      // moves the start-address field (32 bytes = 2 units of 16)
+      const uint64_t dS0 = sdesc(sb, 0u, 1024u), dP0 = sdesc(s_p, 0u, 1024u);
+      constexpr uint64_t kS = S_PIECE >> 4, kPp = P_PIECE >> 4;
       for (int kk = 0; kk < KP / 16; ++kk) {
-#pragma unroll
-        for (int cmb = 0; cmb < 6; ++cmb) {
-          const uint32_t ko = (uint32_t)kk * 32u;
-          mma_bf16(d, sdesc(sb + (uint32_t)kCombA[cmb] * S_PIECE + ko, 0u, 1024u),
-                   sdesc(s_p + (uint32_t)kCombP[cmb] * P_PIECE + ko, 0u, 1024u), IDESC,
-                   (uint32_t)(kk | cmb));
-        }
+        const uint64_t ko = (uint64_t)(2 * kk);
+        // piece products a0p0, a0p1, a1p0, a0p2, a1p1, a2p0
+        mma_bf16(d, dS0 + ko, dP0 + ko, IDESC, (uint32_t)kk);
+        mma_bf16(d, dS0 + ko, dP0 + kPp + ko, IDESC, 1u);
+        mma_bf16(d, dS0 + kS + ko, dP0 + ko, IDESC, 1u);
+        mma_bf16(d, dS0 + ko, dP0 + 2 * kPp + ko, IDESC, 1u);
+        mma_bf16(d, dS0 + kS + ko, dP0 + kPp + ko, IDESC, 1u);
+        mma_bf16(d, dS0 + 2 * kS + ko, dP0 + ko, IDESC, 1u);
       }
       mma_commit(bar(B_DF0 + b));
       mma_commit(bar(B_SE0 + sbuf));

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         // while the converters write the other.
         const int u0 = NP * t, s0 = u0 & 1;
         if ((u0 >> 1) >= 1 &&
-            !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag)) {
+            !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag, 16)) {
           ok = false;
           break;
         }
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         if (NP > 1) {
           const int u1 = u0 + 1;   // slot 1
           if ((u1 >> 1) >= 1 &&
-              !mbar_wait(bar(B_FREE1), ((u1 >> 1) - 1) & 1, S.abort_flag)) {
+              !mbar_wait(bar(B_FREE1), ((u1 >> 1) - 1) & 1, S.abort_flag, 16)) {
             ok = false;
             break;
           }
@@ -600,8 +600,8 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         for (int p = 0; p < NP; ++p) {
           uint32_t pa = pbuf + (uint32_t)p * PIECE_BYTES;
           const int u = NP * t + p;   // TMA form: piece unit u in slot u & 1
-          if (TMA) {
-            if (!mbar_wait(bar(B_FULL0 + (u & 1)), (u >> 1) & 1, S.abort_flag)) {
+          if (TMA) {   // the MMA thread is on the critical path: poll without sleeping
+            if (!mbar_wait_spin(bar(B_FULL0 + (u & 1)), (u >> 1) & 1, S.abort_flag)) {
               ok = false;
               break;
             }
@@ -609,19 +609,24 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
             tc_fence_after();
             pa = S.pieces + (uint32_t)(u & 1) * PIECE_BYTES;
           }
+          // Descriptors: the base ones once per piece; the K steps only move
+          // the start-address field (address >> 4, bits 0-13), which the
+          // constant offsets below never carry out of (shared addresses <
+          // 256 KB), so the single issuing thread spends two integer adds per
+          // MMA instead of rebuilding both descriptors.
+          const uint64_t dA = sdesc(pa, 0u, 2048u), dPsi = sdesc(psi_s, 0u, 2048u);
+          const uint64_t dAy = sdesc(pa, 1024u, 2048u), dOm = sdesc(om, 0u, 2048u);
+          const uint32_t acc0 = (accw >> ct) & 1u;
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {   // W^T: K = 16 rows per instruction
-            const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
-            const uint32_t acc = ((accw >> ct) & 1u) | (uint32_t)(p | kk);
-            mma_bf16(wtm, sdesc(pa + ko, 0u, 2048u), sdesc(psi_s + ko, 0u, 2048u), IDESC_W,
-                     acc);
+            const uint64_t ko = (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);   // bytes >> 4
+            mma_bf16(wtm, dA + ko, dPsi + ko, IDESC_W, acc0 | (uint32_t)(p | kk));
           }
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {   // Y: K = 16 columns per instruction
-            const uint32_t ko = (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u;
-            const uint32_t acc = (uint32_t)(ct | p | kk);
-            mma_bf16(ytm, sdesc(pa + (uint32_t)kk * 4096u, 1024u, 2048u),
-                     sdesc(om + ko, 0u, 2048u), IDESC_Y, acc);
+            const uint64_t ko = (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+            mma_bf16(ytm, dAy + (uint64_t)(kk * 256), dOm + ko, IDESC_Y,
+                     (uint32_t)(ct | p | kk));
           }
           if (TMA) mma_commit(bar(B_FREE0 + (u & 1)));
           TC_TRACE(1, 2 * u + 1);
