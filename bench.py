@@ -518,6 +518,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     bt = IdBatch(probs, stream=stream)
+    tune_choice, tune_ms = bt.tune()     # the project's autotuner: work split of the sketches
     for _ in range(args.warmup):
         bt.run()
     bt.wait()
@@ -561,6 +562,8 @@ def run_batched(args):
                      "bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": "of " + kind,
                      "unit": "GB/s", "frac": gbs / peak, "traffic": None},
         "gpu_launches": launches, "clocks": clk,
+        "autotune": {"rows_per_cta": tune_choice,
+                     "ms_per_launch_by_candidate": {str(k): v for k, v in tune_ms.items()}},
         "k_out_short": sum(1 for (_, _, ko), p in zip(res, spec) if ko < p["k"]),
     }
     print(json.dumps(line))

@@ -281,6 +281,19 @@ id_status id_batch_wait(id_batch* b, int32_t* kout_host);
 /* Synchronise the batch's stream and release everything it holds. */
 void id_batch_destroy(id_batch* b);
 
+/* Autotuner of the batched form: times the batch's graph with each of the
+ * candidate work splits of its sketches (rows_per_cta in {0, 64, 32, 16, 8}:
+ * a problem's sketch runs on at most ceil(row blocks / rows_per_cta) CTAs;
+ * 0 = one CTA per SM) -- one warm-up and three timed replays each, CUDA events
+ * on the batch's private stream -- and keeps the fastest for later
+ * id_batch_run calls (with the same output pointers as here, device).
+ * Outputs: rows_per_cta (the choice, may be NULL), ms (the 5 average replay
+ * times in candidate order, host, may be NULL).  The outputs J, P, kout hold
+ * a complete result of the batch on return.  No counterpart in the paper.
+ * Errors: as id_batch_run. */
+id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout,
+                         int32_t* rows_per_cta, float* ms);
+
 /* ID of the streamed columns with the skeleton chosen among candidates
  * (the learned proposal's): the pivoted QR of W(:, cand) gives J (pivot
  * order, indices of the streamed columns, -1 past k_out), and P (k x n FP64

@@ -95,6 +95,8 @@ SIGNATURES = {
     "id_batch_create": (C.c_int, [C.POINTER(IdBatchProblem), C.c_int32, C.c_void_p,
                                   C.POINTER(C.c_void_p)]),
     "id_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "id_batch_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "id_batch_wait": (C.c_int, [C.c_void_p, C.c_void_p]),
     "id_batch_destroy": (None, [C.c_void_p]),
     "id_mlp_features": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,

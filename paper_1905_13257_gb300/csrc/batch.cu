@@ -48,6 +48,7 @@ struct id_batch {
   int32_t* cap_k = nullptr;
   bool ran = false;
   bool poisoned = false;
+  int rows_per_cta = 0;               // autotuned work split of the sketches (0: one CTA per SM)
 };
 
 namespace {
@@ -165,6 +166,19 @@ id_status capture(id_batch* b, int32_t* J, double* P, int32_t* kout) {
   b->cap_P = P;
   b->cap_k = kout;
   return ID_OK;
+}
+
+// The sketch of problem i runs on at most ceil(row blocks / rows_per_cta)
+// CTAs (rows_per_cta = 0: one per SM, the persistent grid of a single
+// problem); smaller grids let the sketches of several small problems share
+// the GPU instead of each spreading a few row blocks over every SM.
+void apply_split(id_batch* b, int rows_per_cta) {
+  for (size_t i = 0; i < b->prob.size(); ++i) {
+    const int64_t nrb = (b->prob[i].m + 127) / 128;
+    b->h[i]->grid_cap =
+        rows_per_cta > 0 ? (int)std::max<int64_t>(1, (nrb + rows_per_cta - 1) / rows_per_cta) : 0;
+  }
+  b->rows_per_cta = rows_per_cta;
 }
 
 }  // namespace
@@ -290,6 +304,57 @@ id_status id_batch_wait(id_batch* b, int32_t* kout_host) {
   if (kout_host) std::copy(ko.begin(), ko.end(), kout_host);
   for (int i = 0; i < count; ++i)
     if (ko[i] < b->prob[i].k) return ID_ERR_RANK_DEFICIENT;
+  return ID_OK;
+}
+
+id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout,
+                         int32_t* rows_per_cta, float* ms) {
+  if (!b) return ID_ERR_INVALID_ARG;
+  if (b->poisoned) return ID_ERR_CUDA;
+  if (!J || !P || !kout || !is_device_ptr(J) || !is_device_ptr(P) || !is_device_ptr(kout))
+    return ID_ERR_INVALID_ARG;
+  static const int kCand[] = {0, 64, 32, 16, 8};
+  constexpr int kNC = (int)(sizeof(kCand) / sizeof(kCand[0]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail_cuda(b, e);
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  id_status s = ID_OK;
+  for (int c = 0; c < kNC && s == ID_OK; ++c) {
+    apply_split(b, kCand[c]);
+    s = capture(b, J, P, kout);   // the grid sizes are part of the graph
+    if (s != ID_OK) break;
+    // one replay to warm up, then three timed replays on the graph's stream
+    e = cudaGraphLaunch(b->exec, b->origin);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->origin);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->exec, b->origin);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->origin);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) {
+      s = fail_cuda(b, e);
+      break;
+    }
+    t /= 3.f;
+    if (ms) ms[c] = t;
+    if (c == 0 || t < best_ms) {
+      best_ms = t;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != ID_OK) return s;
+  apply_split(b, kCand[best]);
+  s = capture(b, J, P, kout);
+  if (s != ID_OK) return s;
+  if (rows_per_cta) *rows_per_cta = kCand[best];
   return ID_OK;
 }
 

@@ -187,11 +187,12 @@ id_status launch_pending(id_sketch* h) {
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
     a.wpart = h->d_wpart;
+    const int nsm_eff = h->grid_cap > 0 ? std::min(h->grid_cap, h->nsm) : h->nsm;
     if (tc) {
-      IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, h->nsm, h->drain_blocks, h->d_status,
+      IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, nsm_eff, h->drain_blocks, h->d_status,
                                     h->st, h->timer_sketch));
     } else {
-      IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, h->nsm, h->st));
+      IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, nsm_eff, h->st));
     }
     h->y_started = true;
     h->n_launched += taken;

@@ -225,6 +225,7 @@ struct id_sketch {
   bool poisoned = false;
   int sketch_kernel = 0;         // 0 auto, 1 tensor cores, 2 SIMT (IDSKETCH_SKETCH)
   int drain_blocks = 8;          // row blocks between FP64 flushes of W^T (tensor cores)
+  int grid_cap = 0;              // CTAs of a sketch launch at most (0: one per SM)
   int* d_status = nullptr;       // nonzero: a bounded device wait gave up
   float* d_wpart = nullptr;      // per-CTA W^T slabs of the tensor-core sketch
 

@@ -161,3 +161,18 @@ def test_batch_output_pointers_and_errors():
         assert k == k0 and torch.equal(J, J0)
         assert torch.allclose(P, P0, rtol=0, atol=1e-12)
     bt.close()
+
+
+def test_batch_autotuner_keeps_the_results():
+    """id_batch_tune times the candidate work splits, keeps the fastest, and
+    the batch run with it still matches the oracle problem by problem."""
+    from paper_1905_13257_gb300 import IdBatch
+    probs = make_problems(seed0=80)
+    bt = IdBatch(probs)
+    choice, ms = bt.tune()
+    assert choice in ms and all(v > 0 for v in ms.values())
+    assert ms[choice] == min(ms.values())
+    bt.run()
+    for p, (J, P, kout) in zip(probs, bt.wait()):
+        check_against_oracle(p, J, P, kout)
+    bt.close()
