@@ -21,9 +21,12 @@
 //      recomputed from its definition, rows split over the CTAs);
 //   -- grid barrier --
 // A^T v_s = A(s, :)^T + (A^T u below row s) / (u_s - beta) lets the pass over
-// A_c run before the scalars exist, so a step needs two grid barriers.  The arithmetic is that of the
-// multi-launch path in coarse.cu: the passes over rows in FP32 pairs (about
-// 48 bits), scalars, F, R and the norms in FP64, every sum in a fixed order.
+// A_c run before the scalars exist, so a step needs two grid barriers.
+// Arithmetic: the passes over rows and the sums of their per-CTA partials in
+// FP32 pairs (about 48 bits); scalars, F, R and the norms in FP64; every sum
+// in a fixed order.  GB300's FP64 pipe is narrow (a warp's FP64 instruction
+// holds it for about 64 cycles), so nothing per row or per column of a pass
+// runs in FP64.
 //
 // Waits are bounded: a grid barrier or a ring wait that gives up raises the
 // status word; every CTA then leaves its step loop and waits (bounded) for
@@ -45,6 +48,7 @@ constexpr int CW = 16;               // consumer warps
 constexpr int CT = CW * 32;          // consumer threads
 constexpr int NTH = CT + 32;         // + the producer warp
 constexpr int RING = 6;              // stages of the A_c ring
+constexpr int PF_STAGES = 8;         // stages streamed into L2 ahead of the ring loads
 constexpr uint32_t STAGE_MAX = 32768;
 constexpr int QMAX = 128;            // row quads per CTA (512 rows)
 constexpr int HP = kLMax + 1;        // per-CTA partials: V^T u (kLMax), ||u||^2
@@ -84,7 +88,7 @@ struct CoopArgs {
   double* nu20;
   int* colpos;
   int* Jc;
-  double* gpart;        // G x n
+  double* gpart;        // G x n: per-CTA column partials (FP32 pairs, or FP64 in the recompute)
   float2* upart;        // G x HP
   int* rlist;
   int* cint;
@@ -190,6 +194,10 @@ __global__ void __launch_bounds__(NTH, 1)
   __shared__ int pi[CW];
   __shared__ double scal[6];   // alpha, sigma, beta, tau, den, tol
   __shared__ int piv, stop_now, nrec_s;
+  // 1 / (u_s - beta) of the last step, in FP64 and as an FP32 pair: formed once
+  // by thread 0 (an FP64 division per thread costs GB300's narrow FP64 pipe)
+  __shared__ double rden_sh;
+  __shared__ float2 rdf_sh;
 
   const uint32_t ring = (tc::smem_u32(smem_raw) + 127u) & ~127u;
   const uint8_t* ringp = smem_raw + (ring - tc::smem_u32(smem_raw));
@@ -219,6 +227,8 @@ __global__ void __launch_bounds__(NTH, 1)
     abort_flag = 0;
     stop_flag = 0;
     sflag = 0;
+    rden_sh = 0.0;
+    rdf_sh = make_float2(0.f, 0.f);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -234,9 +244,19 @@ __global__ void __launch_bounds__(NTH, 1)
       const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
       const uint64_t keep = tc::policy_evict_last(), stream = tc::policy_evict_first();
       const int64_t total = (int64_t)(1 + a.kmax) * nstage;
-      int64_t u = 0;
+      int64_t u = 0, pf = 1;   // pf: next stage to prefetch into L2
       for (; u < total; ++u) {
         const int slot = (int)(u % RING);
+        // keep PF_STAGES stages ahead of this load on their way into L2 (the
+        // kept columns are there already), so that the ring's loads hit L2
+        // also right after the scalar and column phases of a step
+        for (; pf <= u + PF_STAGES && pf < total; ++pf) {
+          const int pj0 = (int)(pf % nstage) * sgc;
+          if (pj0 >= a.keep_cols) {
+            tc::tma_prefetch_2d(tm, (int)r0, pj0);
+            tc::tma_prefetch_2d(tm, (int)r0 + box_rows, pj0);
+          }
+        }
         if (u >= RING) {
           const uint32_t par = (uint32_t)(((u / RING) - 1) & 1);
           const long long t0 = clock64();
@@ -278,6 +298,7 @@ __global__ void __launch_bounds__(NTH, 1)
 
   // ------------------------------------------------------------ consumers
   int64_t ucons = 0;   // next ring stage to consume
+  float2* const pairs = reinterpret_cast<float2*>(a.gpart);   // the passes' partials
   bool ok = true;
   // One pass over the ring for this CTA's rows: f(column, warp partial pair)
   // receives the warp's FP32-pair sum over the rows of that column.
@@ -323,7 +344,9 @@ __global__ void __launch_bounds__(NTH, 1)
           }
         }
         warp_pair_sum(hi, lo);
-        if (lane == 0) a.gpart[(int64_t)b * n + j0 + c] = (double)hi + (double)lo;
+        // the pair itself: GB300's FP64 units are too narrow for a conversion
+        // per column here (a warp's FP64 instruction holds its pipe ~64 cycles)
+        if (lane == 0) pairs[(int64_t)b * n + j0 + c] = make_float2(hi, lo);
       }
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(empty0 + 8u * slot);
@@ -337,8 +360,12 @@ __global__ void __launch_bounds__(NTH, 1)
   double nsum = 0.0;
   if (ok) {
     for (int j = c0 + tid; j < c1; j += CT) {
-      double s2 = 0.0;
-      for (int bb = 0; bb < G; ++bb) s2 += a.gpart[(int64_t)bb * n + j];
+      float sh = 0.f, sl = 0.f;   // FP32-pair sum over the CTAs, in CTA order
+      for (int bb = 0; bb < G; ++bb) {
+        const float2 x = pairs[(int64_t)bb * n + j];
+        df_add(sh, sl, x.x, x.y);
+      }
+      const double s2 = (double)sh + (double)sl;
       a.nu2[j] = s2;
       a.nu20[j] = s2;
       a.colpos[j] = -1;
@@ -423,11 +450,10 @@ __global__ void __launch_bounds__(NTH, 1)
     CC_TRACE(s, 1);
     const int p = piv;
     for (int t = tid; t < s; t += CT) fp[t] = df_of(a.F[(int64_t)t * a.ldf + p]);
-    const double sig_prev = scal[1], den_prev = scal[4];
     cons_sync();
     // v_{s-1} from u_{s-1}, then u = A(:, p) - V_s F(p, :)^T for this CTA's rows
     float2 sig = make_float2(0.f, 0.f);
-    const float2 prcp = df_of((s > 0 && sig_prev != 0.0) ? 1.0 / den_prev : 0.0);
+    const float2 prcp = rdf_sh;   // 1 / (u_{s-1} - beta_{s-1}); zero at s = 0
     for (int rr = tid; rr < nrows; rr += CT) {
       const int64_t i = r0 + rr;
       if (s > 0) {
@@ -439,7 +465,7 @@ __global__ void __launch_bounds__(NTH, 1)
       }
       float2 u = make_float2(0.f, 0.f);
       if (i >= s) {
-        u = df_of((double)a.Ac[i + (int64_t)p * mc]);
+        u = make_float2(a.Ac[i + (int64_t)p * mc], 0.f);
         for (int t0 = 0; t0 < s; t0 += 16) {
           float2 vv[16];
 #pragma unroll
@@ -552,6 +578,8 @@ __global__ void __launch_bounds__(NTH, 1)
       scal[2] = beta;
       scal[3] = tau;
       scal[4] = den;
+      rden_sh = sigma != 0.0 ? 1.0 / den : 0.0;
+      rdf_sh = df_of(rden_sh);
       if (b == 0) {
         a.cscal[CS_ALPHA] = alpha;
         a.cscal[CS_SIGMA] = sigma;
@@ -563,7 +591,7 @@ __global__ void __launch_bounds__(NTH, 1)
     }
     cons_sync();
     {
-      const double rden = scal[1] != 0.0 ? 1.0 / scal[4] : 0.0;
+      const double rden = rden_sh;
       for (int t = tid; t < s; t += CT) {
         const double vst = df_val(a.V[(int64_t)t * mc + s]);   // v_t[s]
         hvec[t] = vst + hs[t] * rden;
@@ -577,20 +605,25 @@ __global__ void __launch_bounds__(NTH, 1)
     {
       const double tau = scal[3], den = scal[4], sigma = scal[1];
       for (int j = c0 + warp; j < c1; j += CW) {
-        double gv[8], fv[2];   // every load of the lane in flight (G <= 256, s <= 64)
+        float2 gv[8];   // every load of the lane in flight (G <= 256, s <= 64)
+        double fv[2];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int bb = lane + 32 * e;
-          gv[e] = bb < G ? a.gpart[(int64_t)bb * n + j] : 0.0;
+          gv[e] = bb < G ? pairs[(int64_t)bb * n + j] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int t = lane + 32 * e;
           fv[e] = t < s ? a.F[(int64_t)t * a.ldf + j] : 0.0;
         }
-        double gs = 0.0;
+        // (A^T u)_j: the CTAs' FP32-pair partials summed as FP32 pairs (lane
+        // order, then a fixed shuffle tree), one FP64 value at the end
+        float gh = 0.f, gl = 0.f;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) gs += gv[e];
+        for (int e = 0; e < 8; ++e) df_add(gh, gl, gv[e].x, gv[e].y);
+        warp_pair_sum(gh, gl);
+        const double gs = (double)gh + (double)gl;
         double fh = 0.0, rr = 0.0;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -602,7 +635,6 @@ __global__ void __launch_bounds__(NTH, 1)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          gs += __shfl_xor_sync(0xffffffffu, gs, o);
           fh += __shfl_xor_sync(0xffffffffu, fh, o);
           rr += __shfl_xor_sync(0xffffffffu, rr, o);
         }
@@ -639,7 +671,7 @@ __global__ void __launch_bounds__(NTH, 1)
     cons_sync();
     const int nrec = nrec_s;
     if (nrec > 0) {
-      const double rden = scal[1] != 0.0 ? 1.0 / scal[4] : 0.0;
+      const double rden = rden_sh;
       for (int idx = 0; idx < nrec; ++idx) {
         const int j = a.rlist[idx];
         double ssum = 0.0;

@@ -293,6 +293,29 @@ def test_recon_error_small_residual_fp32(k):
     sk.close()
 
 
+@pytest.mark.parametrize("m,n,k", [(3000, 120, 12), (64 * 9 + 17, 300, 40)])
+def test_recon_error_zero_entries_fp32(m, n, k):
+    """Entries with A_ij = 0 are left out of the entry-wise metric (Sec. 3.1):
+    about one entry in a hundred set to zero (their residuals are not zero,
+    so the kernel's reciprocal of A_ij is infinite there), and a band of
+    zero rows (residual zero as well)."""
+    A = gaussian_matrix(m, n, seed=m + 7, dtype=torch.float32, device=DEV)
+    A = A + low_rank_matrix(m, n, 4, seed=2, dtype=torch.float32, device=DEV) * 10
+    g = np.random.default_rng(m)
+    mask = torch.as_tensor(g.random((m, n)) < 0.01, device=DEV)
+    A[mask] = 0.0
+    A[100:140, :] = 0.0
+    J = torch.tensor(g.choice(n, size=k, replace=False), dtype=torch.int32)
+    P = torch.tensor(g.normal(size=(k, n)) * 0.3)
+    sk = _sk(m=m, n_max=n, k=k, l=64, seed=0, dtype=torch.float32)
+    fro, mx = sk.reconstruct_error(A, J, P)
+    fo, mo = oracle.recon_error(A.cpu().double().numpy(), J.numpy(), P.numpy())
+    assert np.isfinite(mx)
+    assert abs(fro - fo) <= err_tol(fo, torch.float32)
+    assert abs(mx - mo) <= err_tol(mo, torch.float32)
+    sk.close()
+
+
 def test_recon_error_invalid_arguments():
     from paper_1905_13257_gb300 import IdError
     A = gaussian_matrix(100, 10, seed=1, dtype=torch.float32, device=DEV)
