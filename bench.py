@@ -705,6 +705,8 @@ def main():
     ap.add_argument("--n", type=int, default=NSNAP)
     ap.add_argument("--grid", type=str, default=None,
                     help="nx,ny,nz of a smaller case (profiling); default 128,96,128")
+    ap.add_argument("--coarse-stride", type=str, default=None,
+                    help="sx,sy,sz of the coarse grid (profiling); default 4,4,4")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-planes", type=int, default=8,
@@ -724,6 +726,9 @@ def main():
                     help="y-planes of component u per step of the reference arm's sample "
                          "(the same sample as cpu_baseline by default)")
     args = ap.parse_args()
+    if args.coarse_stride:
+        global STRIDE
+        STRIDE = tuple(int(x) for x in args.coarse_stride.split(","))
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -397,6 +397,21 @@ void id_sketch_destroy(id_sketch* h);
 id_status id_timing_enable(id_sketch* h, int32_t on);
 id_status id_timing_read(id_sketch* h, int32_t which, double* total_ms, int64_t* launches);
 
+/* Self-check of the device-side bounded waits, a fault-handling aid with no
+ * counterpart in the paper.  Every wait in this library's kernels (mbarrier
+ * phases, the coarse QR's grid barrier) gives up after a limit and raises a
+ * status word that the host turns into ID_ERR_TIMEOUT, so that a stuck
+ * kernel returns instead of hanging the GPU.  This call runs those same wait
+ * routines, instantiated with a limit of about 1 ms, on device `device`:
+ *   mode 0: an mbarrier phase that nothing completes   -> ID_ERR_TIMEOUT
+ *   mode 1: the same phase, completed before the wait -> ID_OK
+ *   mode 2: the grid barrier of a cooperative launch of 2 CTAs, one of which
+ *           never reaches it                           -> ID_ERR_TIMEOUT
+ *   mode 3: the same barrier reached by both CTAs       -> ID_OK
+ * Nothing faults and the context stays usable.  Synchronous (its own
+ * stream).  Errors: ID_ERR_INVALID_ARG (mode), ID_ERR_CUDA. */
+id_status id_check_wait(int32_t device, int32_t mode);
+
 /* Fill out[(i - first) * width + s] = G(i, s) for i in [first, first+count),
  * s in [0, width): the same counter-based Gaussian entries the sketch uses,
  * which = 1 for Psi (G(i,s) = Psi[s, i]) and which = 2 for Omega

@@ -8,8 +8,9 @@ variant and the single-pass ID, measures the reconstruction error in one more
 read, and runs batches of independent matrices in one graph launch.  The C ABI
 is include/idsketch.h; ``api`` wraps it for PyTorch tensors.
 """
-from .api import IdBatch, IdSketch, Mlp, gaussian_fill, gaussian_table_bits, mlp_features
+from .api import (IdBatch, IdSketch, Mlp, check_wait, gaussian_fill, gaussian_table_bits,
+                  mlp_features)
 from ._binding import load, IdError
 
-__all__ = ["IdBatch", "IdSketch", "Mlp", "gaussian_fill", "gaussian_table_bits",
-           "mlp_features", "load", "IdError"]
+__all__ = ["IdBatch", "IdSketch", "Mlp", "check_wait", "gaussian_fill",
+           "gaussian_table_bits", "mlp_features", "load", "IdError"]

@@ -119,6 +119,7 @@ SIGNATURES = {
     "id_gaussian_fill": (C.c_int, [C.c_int32, C.c_uint64, C.c_int64, C.c_int64, C.c_int32,
                                    C.c_void_p, C.c_void_p]),
     "id_gaussian_table": (C.c_int, [C.POINTER(C.c_uint16)]),
+    "id_check_wait": (C.c_int, [C.c_int32, C.c_int32]),
     "id_kernel_launches": (C.c_int64, []),
     "id_last_cuda_error": (C.c_char_p, []),
     "id_status_str": (C.c_char_p, [C.c_int]),

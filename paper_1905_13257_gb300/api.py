@@ -388,3 +388,13 @@ def gaussian_table_bits():
     buf = (C.c_uint16 * 4096)()
     B.check(lib.id_gaussian_table(buf), "id_gaussian_table")
     return [int(x) for x in buf]
+
+
+def check_wait(mode, device=0):
+    """Self-check of the device-side bounded waits (id_check_wait): returns the
+    status code (ID_OK = 0, ID_ERR_TIMEOUT = 6); raises IdError on any other."""
+    lib = B.load()
+    st = lib.id_check_wait(int(device), int(mode))
+    if st not in (0, 6):
+        B.check(st, "id_check_wait")
+    return st

@@ -715,6 +715,26 @@ id_status id_timing_read(id_sketch* h, int32_t which, double* total_ms, int64_t*
   return ID_OK;
 }
 
+id_status id_check_wait(int32_t device, int32_t mode) {
+  if (mode < 0 || mode > 3) return ID_ERR_INVALID_ARG;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+    g_last_cuda_error.store((int)cudaGetLastError());
+    return ID_ERR_CUDA;
+  }
+  cudaStream_t st = nullptr;
+  int gave_up = 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = idsk::run_wait_check(mode, st, &gave_up);
+  if (st) cudaStreamDestroy(st);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    g_last_cuda_error.store((int)e);
+    return ID_ERR_CUDA;
+  }
+  return gave_up ? ID_ERR_TIMEOUT : ID_OK;
+}
+
 void id_sketch_destroy(id_sketch* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);

@@ -10,9 +10,10 @@
 //      column s-1 of V into v_{s-1}; for the CTA's rows
 //        u = A(:, p) - V_s F(p, :)^T     (rows >= s; kept as column s of V),
 //      the CTA's partials of V_s^T u and ||u||^2 (rows > s), and its share
-//      of A^T u: its rows of every column, streamed from HBM in TMA boxes
-//      through a shared-memory ring (the producer warp runs ahead across
-//      steps: A_c does not change), one partial per (CTA, column);
+//      of A^T u: its rows of every column (warp w takes columns w, w + 16,
+//      ...; 128-bit loads two columns ahead of the sums, so that the warps
+//      stream A_c independently of one another), one partial per (CTA,
+//      column);
 //   -- grid barrier --
 //   B  every CTA sums the partials (in CTA order) into the Householder
 //      scalars alpha = u_s, beta, tau, den = alpha - beta and h = V_s^T v_s;
@@ -28,9 +29,8 @@
 // holds it for about 64 cycles), so nothing per row or per column of a pass
 // runs in FP64.
 //
-// Waits are bounded: a grid barrier or a ring wait that gives up raises the
-// status word; every CTA then leaves its step loop and waits (bounded) for
-// its own bulk copies before it exits.
+// Waits are bounded: a grid barrier that gives up raises the status word, and
+// every CTA then leaves its step loop.
 #include <float.h>
 #include <stdlib.h>
 #include <string.h>
@@ -45,11 +45,8 @@ namespace idsk {
 namespace {
 
 constexpr int CW = 16;               // consumer warps
-constexpr int CT = CW * 32;          // consumer threads
-constexpr int NTH = CT + 32;         // + the producer warp
-constexpr int RING = 6;              // stages of the A_c ring
-constexpr int PF_STAGES = 8;         // stages streamed into L2 ahead of the ring loads
-constexpr uint32_t STAGE_MAX = 32768;
+constexpr int CT = CW * 32;          // threads (all of them consumers of the passes)
+constexpr int NTH = CT;
 constexpr int QMAX = 128;            // row quads per CTA (512 rows)
 constexpr int HP = kLMax + 1;        // per-CTA partials: V^T u (kLMax), ||u||^2
 constexpr double kRecomputeFrac = 1.0 / (1 << 20);
@@ -94,11 +91,30 @@ struct CoopArgs {
   int* cint;
   double* cscal;
   int* status;
-  int keep_cols;        // columns whose ring loads are kept in L2 (evict_last)
-  int sgc;              // columns per ring stage
-  int box_rows;         // rows per TMA box (two boxes cover a CTA's rows)
+  int keep_cols;        // leading columns whose loads are kept in L2 (evict_last)
   double tol_factor;
 };
+
+// 128-bit read-only load with an L2 cache policy (createpolicy).  With
+// IDSK_CC_L1NA the lines are not allocated in L1, which then keeps the CTA's
+// rows of V (re-read by every step's u and V^T u phases) instead of the
+// stream of A_c.
+#ifndef IDSK_CC_L1NA
+#define IDSK_CC_L1NA 0
+#endif
+__device__ __forceinline__ float4 ld_f4_hint(const float* p, uint64_t policy) {
+  float4 v;
+#if IDSK_CC_L1NA
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(policy));
+#else
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(policy));
+#endif
+  return v;
+}
 
 __device__ __forceinline__ unsigned long long norm_key(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -110,8 +126,9 @@ __device__ __forceinline__ void cons_sync() {
 }
 
 // Grid-wide barrier of the consumer threads of every CTA (cooperative
-// launch: all CTAs are resident).  Bounded: false when it gave up (or another
-// CTA did), with the status word raised.
+// launch: all CTAs are resident).  Bounded (LIMIT clock64 cycles): false when
+// it gave up (or another CTA did), with the status word raised.
+template <long long LIMIT = tc::kWaitCycles>
 __device__ bool grid_sync(const CoopArgs& a, int* sflag) {
   cons_sync();
   if (threadIdx.x == 0) {
@@ -130,7 +147,7 @@ __device__ bool grid_sync(const CoopArgs& a, int* sflag) {
           *sflag = 1;
           break;
         }
-        if (clock64() - t0 > tc::kWaitCycles) {
+        if (clock64() - t0 > LIMIT) {
           atomicOr(a.status, 1);
           *sflag = 1;
           break;
@@ -181,10 +198,8 @@ __device__ __forceinline__ void warp_pair_sum(float& h, float& l) {
 }
 
 __global__ void __launch_bounds__(NTH, 1)
-    coarse_coop_kernel(CoopArgs a, const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * RING];
-  __shared__ int abort_flag, stop_flag, sflag;
+    coarse_coop_kernel(CoopArgs a) {
+  __shared__ int sflag;
   __shared__ __align__(16) float uhs[QMAX * 4];
   __shared__ __align__(16) float uls[QMAX * 4];
   __shared__ float2 fp[kLMax];
@@ -199,10 +214,6 @@ __global__ void __launch_bounds__(NTH, 1)
   __shared__ double rden_sh;
   __shared__ float2 rdf_sh;
 
-  const uint32_t ring = (tc::smem_u32(smem_raw) + 127u) & ~127u;
-  const uint8_t* ringp = smem_raw + (ring - tc::smem_u32(smem_raw));
-  const uint32_t full0 = tc::smem_u32(&bars[0]), empty0 = tc::smem_u32(&bars[RING]);
-  const uint32_t abort_a = tc::smem_u32(&abort_flag);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x, b = blockIdx.x;
   const int64_t mc = a.mc;
@@ -213,143 +224,75 @@ __global__ void __launch_bounds__(NTH, 1)
   const int nrows = (int)(4 * (q1 - q0));
   const int nq = (int)(q1 - q0);
   const int c0 = (int)((int64_t)n * b / G), c1 = (int)((int64_t)n * (b + 1) / G);
-  const int sgc = a.sgc;
-  const int box_rows = a.box_rows;
-  const uint32_t box_bytes = (uint32_t)(box_rows * sgc * 4);
-  const int nstage = (n + sgc - 1) / sgc;
-  const uint32_t stage_bytes = 2u * box_bytes;
 
   if (tid == 0) {
-    for (int q = 0; q < RING; ++q) {
-      tc::mbar_init(full0 + 8u * q, 1);
-      tc::mbar_init(empty0 + 8u * q, CW);
-    }
-    abort_flag = 0;
-    stop_flag = 0;
     sflag = 0;
     rden_sh = 0.0;
     rdf_sh = make_float2(0.f, 0.f);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == CW) {
-    // ------------------------------------------------------------ producer
-    // Stage u holds columns [sgc * (u % nstage), ...) of this CTA's rows, for
-    // pass u / nstage (pass 0: the norms, pass 1 + s: step s), as two TMA
-    // boxes of box_rows rows x sgc columns (column-major, zero fill past the
-    // matrix).  A_c does not change, so the producer runs ahead across steps,
-    // bounded by the ring.
-    if (lane == 0) {
-      const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
-      const uint64_t keep = tc::policy_evict_last(), stream = tc::policy_evict_first();
-      const int64_t total = (int64_t)(1 + a.kmax) * nstage;
-      int64_t u = 0, pf = 1;   // pf: next stage to prefetch into L2
-      for (; u < total; ++u) {
-        const int slot = (int)(u % RING);
-        // keep PF_STAGES stages ahead of this load on their way into L2 (the
-        // kept columns are there already), so that the ring's loads hit L2
-        // also right after the scalar and column phases of a step
-        for (; pf <= u + PF_STAGES && pf < total; ++pf) {
-          const int pj0 = (int)(pf % nstage) * sgc;
-          if (pj0 >= a.keep_cols) {
-            tc::tma_prefetch_2d(tm, (int)r0, pj0);
-            tc::tma_prefetch_2d(tm, (int)r0 + box_rows, pj0);
-          }
-        }
-        if (u >= RING) {
-          const uint32_t par = (uint32_t)(((u / RING) - 1) & 1);
-          const long long t0 = clock64();
-          bool ok = true;
-          while (!tc::mbar_try(empty0 + 8u * slot, par)) {
-            if (*(volatile int*)&stop_flag || *(volatile int*)&abort_flag) {
-              ok = false;
-              break;
-            }
-            if (clock64() - t0 > tc::kWaitCycles) {
-              tc::st_volatile_shared(abort_a, 1);
-              ok = false;
-              break;
-            }
-          }
-          if (!ok) break;
-        }
-        const int st = (int)(u % nstage);
-        const int j0 = st * sgc;
-        const uint64_t pol = j0 < a.keep_cols ? keep : stream;
-        tc::mbar_expect_tx(full0 + 8u * slot, stage_bytes);
-        tc::tma_load_2d(ring + (uint32_t)slot * stage_bytes, tm, (int)r0, j0, full0 + 8u * slot,
-                        pol);
-        tc::tma_load_2d(ring + (uint32_t)slot * stage_bytes + box_bytes, tm, (int)r0 + box_rows,
-                        j0, full0 + 8u * slot, pol);
-      }
-      // every issued copy has landed before the CTA exits (bounded)
-      const int64_t issued = u;
-      const int64_t first = issued > RING ? issued - RING : 0;
-      for (int64_t v = first; v < issued; ++v) {
-        const int slot = (int)(v % RING);
-        const long long t0 = clock64();
-        while (!tc::mbar_try(full0 + 8u * slot, (uint32_t)((v / RING) & 1)))
-          if (clock64() - t0 > tc::kWaitCycles) break;
-      }
-    }
-    return;
-  }
-
   // ------------------------------------------------------------ consumers
-  int64_t ucons = 0;   // next ring stage to consume
   float2* const pairs = reinterpret_cast<float2*>(a.gpart);   // the passes' partials
   bool ok = true;
-  // One pass over the ring for this CTA's rows: f(column, warp partial pair)
-  // receives the warp's FP32-pair sum over the rows of that column.
-  // mode 0: sum of squares; mode 1: A^T u with u from uhs / uls.
+  // One pass over A_c for this CTA's rows: warp w takes columns w, w + CW,
+  // ...; lane l loads row quads l, l + 32, ... of a column (128-bit loads,
+  // the leading keep_cols columns with an evict-last L2 policy), two columns
+  // ahead of the FP32-pair sums; each column's sum goes to its slot of the
+  // CTA's partials.  mode 0: sums of squares; mode 1: A^T u with u from
+  // uhs / uls.  Columns at or past n load nothing.
   auto pass = [&](int mode) -> bool {
     float4 uh4[QMAX / 32], ul4[QMAX / 32];
-    if (mode == 1) {
+#pragma unroll
+    for (int e = 0; e < QMAX / 32; ++e) {
+      const int q = lane + 32 * e;
+      const bool in = mode == 1 && q < nq;
+      uh4[e] = in ? *reinterpret_cast<const float4*>(&uhs[4 * q]) : make_float4(0, 0, 0, 0);
+      ul4[e] = in ? *reinterpret_cast<const float4*>(&uls[4 * q]) : make_float4(0, 0, 0, 0);
+    }
+    const uint64_t keep = tc::policy_evict_last(), stream = tc::policy_evict_first();
+    auto load_col = [&](int j, float4 (&x)[QMAX / 32]) {
+      const float* colp = a.Ac + (int64_t)j * mc + r0;
+      const uint64_t pol = j < a.keep_cols ? keep : stream;
 #pragma unroll
       for (int e = 0; e < QMAX / 32; ++e) {
         const int q = lane + 32 * e;
-        uh4[e] = q < nq ? *reinterpret_cast<const float4*>(&uhs[4 * q]) : make_float4(0, 0, 0, 0);
-        ul4[e] = q < nq ? *reinterpret_cast<const float4*>(&uls[4 * q]) : make_float4(0, 0, 0, 0);
+        x[e] = (j < n && q < nq) ? ld_f4_hint(colp + 4 * q, pol) : make_float4(0, 0, 0, 0);
       }
-    }
-    for (int st = 0; st < nstage; ++st, ++ucons) {
-      const int slot = (int)(ucons % RING);
-      if (!tc::mbar_wait_spin(full0 + 8u * slot, (uint32_t)((ucons / RING) & 1), abort_a))
-        return false;
-      const int j0 = st * sgc;
-      const int ncols = min(sgc, n - j0);
-      for (int c = warp; c < ncols; c += CW) {
-        // row quad q of column c: box 0 (rows < box_rows) or box 1
-        const uint8_t* col0 = ringp + (size_t)slot * stage_bytes + (size_t)c * box_rows * 4;
-        const uint8_t* col1 = col0 + box_bytes - (size_t)box_rows * 4;
-        float hi = 0.f, lo = 0.f;
+    };
+    auto col_sum = [&](const float4 (&x)[QMAX / 32], int j) {
+      float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int e = 0; e < QMAX / 32; ++e) {
-          const int q = lane + 32 * e;
-          if (q < nq) {
-            const float4 x = *reinterpret_cast<const float4*>(
-                4 * q < box_rows ? col0 + 16 * q : col1 + 16 * q);
-            if (mode == 0) {
-              df_acc(hi, lo, x.x, x.x, 0.f);
-              df_acc(hi, lo, x.y, x.y, 0.f);
-              df_acc(hi, lo, x.z, x.z, 0.f);
-              df_acc(hi, lo, x.w, x.w, 0.f);
-            } else {
-              df_acc(hi, lo, x.x, uh4[e].x, ul4[e].x);
-              df_acc(hi, lo, x.y, uh4[e].y, ul4[e].y);
-              df_acc(hi, lo, x.z, uh4[e].z, ul4[e].z);
-              df_acc(hi, lo, x.w, uh4[e].w, ul4[e].w);
-            }
+      for (int e = 0; e < QMAX / 32; ++e) {
+        if (lane + 32 * e < nq) {
+          if (mode == 0) {
+            df_acc(hi, lo, x[e].x, x[e].x, 0.f);
+            df_acc(hi, lo, x[e].y, x[e].y, 0.f);
+            df_acc(hi, lo, x[e].z, x[e].z, 0.f);
+            df_acc(hi, lo, x[e].w, x[e].w, 0.f);
+          } else {
+            df_acc(hi, lo, x[e].x, uh4[e].x, ul4[e].x);
+            df_acc(hi, lo, x[e].y, uh4[e].y, ul4[e].y);
+            df_acc(hi, lo, x[e].z, uh4[e].z, ul4[e].z);
+            df_acc(hi, lo, x[e].w, uh4[e].w, ul4[e].w);
           }
         }
-        warp_pair_sum(hi, lo);
-        // the pair itself: GB300's FP64 units are too narrow for a conversion
-        // per column here (a warp's FP64 instruction holds its pipe ~64 cycles)
-        if (lane == 0) pairs[(int64_t)b * n + j0 + c] = make_float2(hi, lo);
       }
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(empty0 + 8u * slot);
+      warp_pair_sum(hi, lo);
+      if (lane == 0) pairs[(int64_t)b * n + j] = make_float2(hi, lo);
+    };
+    float4 x0[QMAX / 32], x1[QMAX / 32], x2[QMAX / 32];
+    load_col(warp, x0);
+    load_col(warp + CW, x1);
+    for (int j = warp; j < n; j += 3 * CW) {
+      load_col(j + 2 * CW, x2);
+      col_sum(x0, j);
+      if (j + CW >= n) break;
+      load_col(j + 3 * CW, x0);
+      col_sum(x1, j + CW);
+      if (j + 2 * CW >= n) break;
+      load_col(j + 4 * CW, x1);
+      col_sum(x2, j + 2 * CW);
     }
     return true;
   };
@@ -712,8 +655,40 @@ __global__ void __launch_bounds__(NTH, 1)
     for (int q = kout + tid; q < a.k; q += CT) a.Jc[q] = -1;
   }
   if (!ok && tid == 0) atomicOr(a.status, 1);
-  // release the producer (it may wait for ring slots nobody will consume)
-  if (tid == 0) tc::st_volatile_shared(tc::smem_u32(&stop_flag), 1);
+}
+
+// ------------------------------------------------------------------------
+// Self-check of the bounded waits' give-up path (no fault, no hang): the
+// waits of the kernels above, instantiated with a limit of ~1 ms, on a phase
+// or a barrier that nothing completes, and the same waits on one that
+// completes.  The status word is raised exactly as in the real kernels.
+constexpr long long kCheckWaitCycles = 1ll << 21;
+__device__ int g_check_words[8];   // barrier counters (CI_BAR_*) and, in slot 7, the status
+
+// One CTA waits on phase 0 of an mbarrier; `complete`: thread 0 arrives
+// first (the phase completes), else nobody does.
+__global__ void mbar_check_kernel(int complete, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  const uint32_t b = tc::smem_u32(&bar), af = tc::smem_u32(&abort_flag);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(b, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (complete && threadIdx.x == 0) tc::mbar_arrive(b);
+  if (!tc::mbar_wait<kCheckWaitCycles>(b, 0, af)) atomicOr(status, 1);
+}
+
+// The coarse kernel's grid barrier over a cooperative launch; `skip`: the
+// last CTA returns without reaching it.
+__global__ void __launch_bounds__(CT, 1) grid_check_kernel(CoopArgs a, int skip) {
+  __shared__ int sflag;
+  if (threadIdx.x == 0) sflag = 0;
+  __syncthreads();
+  if (skip && blockIdx.x == gridDim.x - 1) return;
+  if (!grid_sync<kCheckWaitCycles>(a, &sflag) && threadIdx.x == 0) atomicOr(a.status, 1);
 }
 
 }  // namespace
@@ -743,11 +718,41 @@ bool coarse_coop_ok(const id_sketch* h) {
   return Q >= 1 && G <= 256 && (Q + G - 1) / G <= QMAX && h->coarse_blocks >= G;
 }
 
+// Runs one self-check of the bounded waits (modes as id_check_wait) on
+// stream st; *gave_up = 1 when the wait gave up and raised the status word.
+cudaError_t run_wait_check(int mode, cudaStream_t st, int* gave_up) {
+  int* words = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&words, g_check_words);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(words, 0, sizeof(g_check_words), st)) != cudaSuccess) return e;
+  if (mode == 0 || mode == 1) {
+    mbar_check_kernel<<<1, 32, 0, st>>>(mode == 1, words + 7);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    CoopArgs a;
+    memset(&a, 0, sizeof(a));
+    a.cint = words;
+    a.status = words + 7;
+    int skip = mode == 2;
+    void* args[] = {&a, &skip};
+    e = cudaLaunchCooperativeKernel((const void*)grid_check_kernel, dim3(2), dim3(CT), args, 0,
+                                   st);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  int h = 0;
+  if ((e = cudaMemcpyAsync(&h, words + 7, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  *gave_up = h != 0;
+  return cudaSuccess;
+}
+
 cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
   const int n = (int)n64;
   const int64_t Q = h->mc / 4;
   const int G = (int)std::min<int64_t>(h->nsm, Q);   // every CTA owns a row quad
-  const int64_t qmax = (Q + G - 1) / G;
   CoopArgs a;
   a.Ac = reinterpret_cast<const float*>(h->d_Ac);
   a.mc = h->mc;
@@ -768,12 +773,6 @@ cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
   a.cint = h->d_cint;
   a.cscal = h->d_cscal;
   a.status = h->d_status;
-  a.box_rows = (int)(4 * ((qmax + 1) / 2));   // two boxes of at most 256 rows
-  a.sgc = (int)std::max<int64_t>(1, std::min<int64_t>(16, STAGE_MAX / (8 * a.box_rows)));
-  CUtensorMap tm;
-  memset(&tm, 0, sizeof(tm));
-  if (!make_tmap_f32_2d(h->d_Ac, h->mc, n, h->mc, a.box_rows, a.sgc, &tm))
-    return cudaErrorNotSupported;   // the multi-launch path serves it
   a.tol_factor = ID_RANK_TOL_FACTOR;
   int l2 = 0;
   if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev) != cudaSuccess) {
@@ -782,14 +781,11 @@ cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
   }
   // about 3/8 of L2 holds the leading columns of A_c from one step to the next
   a.keep_cols = (int)std::min<int64_t>(n, (int64_t)(0.375 * l2 / (4.0 * (double)h->mc)));
-  const size_t smem = 128 + (size_t)RING * 8 * a.box_rows * a.sgc;
-  cudaError_t e = cudaFuncSetAttribute(coarse_coop_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaMemsetAsync(h->d_cint, 0, 8 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(h->d_cint, 0, 8 * sizeof(int), st)) != cudaSuccess) return e;
-  void* args[] = {&a, &tm};
-  e = cudaLaunchCooperativeKernel((const void*)coarse_coop_kernel, dim3(G), dim3(NTH), args,
-                                  smem, st);
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void*)coarse_coop_kernel, dim3(G), dim3(NTH), args, 0,
+                                  st);
   if (e != cudaSuccess) return e;
   count_launches(1);
   return launch_solve_p(h->d_Rc, h->d_Jc, h->d_colposc, h->d_cint + CI_KOUT, h->k, n, h->d_Pc,

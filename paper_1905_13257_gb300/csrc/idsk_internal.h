@@ -293,6 +293,7 @@ cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
 // multiple of 4, at most 512 rows per CTA.
 bool coarse_coop_ok(const id_sketch* h);
 cudaError_t launch_coarse_coop(id_sketch* h, int64_t n, cudaStream_t st);
+cudaError_t run_wait_check(int mode, cudaStream_t st, int* gave_up);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
                                double* out3, int* status, cudaStream_t st,

@@ -14,7 +14,7 @@
 // precision form.  The tensor cores' FP32 accumulator error grows with the
 // length of the sum, so W^T partials leave TMEM every few row blocks; they
 // are added (round to nearest) into a per-CTA FP32 slab, about 30 partials
-// per entry, and the slabs are summed in FP64.
+// per entry, and the slabs are summed in FP32 pairs (about 48 bits).
 //
 // Shared-memory layout.  A piece tile is stored in 128-byte-swizzled 1 KB
 // atoms of 8 columns x 64 rows (rows contiguous).  Read as K-major it is the
@@ -25,7 +25,7 @@
 // Warp roles (one CTA per SM, persistent over a contiguous range of row
 // blocks):
 //   warps 0-7    converters: load A with 128-bit coalesced loads in half
-//                tiles (three register buffers: two half tiles in flight),
+//                tiles (two register buffers: one half tile in flight),
 //                split into pieces, store them to the swizzled piece buffer
 //                (double-buffered), gather coarse rows
 //   warps 8-11   epilogue: draw Psi for upcoming row blocks (counter
@@ -35,8 +35,14 @@
 //                is handed back to the MMAs as soon as it is in registers,
 //                before its reductions)
 //   warp 12      TMEM allocation and the single-thread tcgen05.mma issue
-// 13 warps keep at most 4 warps per SM sub-partition, so a thread may hold
-// up to 128 registers.
+//   warp 13      (TMA form: a single-segment window with 16-byte aligned
+//                columns) streams raw FP32 boxes of 128 rows x 32 columns
+//                through an NST-stage shared-memory ring; the converters
+//                then read A from the ring and fill two single-piece slots
+//                in turn, so that the MMAs of one piece overlap the
+//                conversion of the other
+// At most 4 warps per SM sub-partition, so a thread may hold up to 128
+// registers.
 // Every mbarrier wait is bounded: on timeout the CTA raises an abort flag,
 // every role leaves its loop, in-flight MMAs are waited for (bounded) and the
 // TMEM is freed; the host reads the status word and reports ID_ERR_TIMEOUT.
@@ -47,6 +53,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "idsk_internal.h"
 #include "tc_common.cuh"
 
@@ -687,21 +694,33 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   if (tid == 0 && ld_volatile_shared(S.abort_flag)) atomicOr(status, 1);
 }
 
-// W(:, window) = sum over CTAs of their slabs, in FP64 and CTA order
-// (deterministic).  A CTA whose row range is empty never wrote its slab and
-// is skipped.
+// W(:, window) = sum over CTAs of their slabs, in CTA order (deterministic),
+// as FP32 pairs (about 48 bits; GB300's FP64 pipe is too narrow for 152
+// dependent FP64 additions per entry), eight slabs' loads in flight at a
+// time.  A CTA whose row range is empty never wrote its slab and is skipped
+// (only possible when there are fewer row blocks than CTAs).
 __global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, int l, int ncols,
                                     int64_t nrb, double* __restrict__ W, int64_t ldw,
                                     int64_t col_base) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * ncols) return;
   const int c = e / l, s = e - c * l;
-  double acc = 0.0;
-  for (int b = 0; b < nslab; ++b) {
-    if (nrb * (b + 1) / nslab == nrb * b / nslab) continue;
-    acc += (double)wpart[((int64_t)b * (kTcMaxTiles * TCOLS) + c) * LP + s];
+  const float* src = wpart + (int64_t)c * LP + s;
+  const int64_t slab = (int64_t)kTcMaxTiles * TCOLS * LP;
+  const bool all_rows = nrb >= nslab;   // then every CTA owns at least one row block
+  float hi = 0.f, lo = 0.f;
+  for (int b0 = 0; b0 < nslab; b0 += 8) {
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = b0 + q;
+      const bool used = b < nslab && (all_rows || nrb * (b + 1) / nslab != nrb * b / nslab);
+      x[q] = used ? src[(int64_t)b * slab] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) df_add(hi, lo, x[q], 0.f);
   }
-  W[(int64_t)s * ldw + col_base + c] = acc;
+  W[(int64_t)s * ldw + col_base + c] = (double)hi + (double)lo;
 }
 
 template <int NP, bool TMA>

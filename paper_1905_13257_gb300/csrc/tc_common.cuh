@@ -49,13 +49,18 @@ __device__ __forceinline__ void st_volatile_shared(uint32_t a, int v) {
 // The first poll is inline; the polling loop is out of line, so that a
 // kernel with many wait sites stays small (warp-specialised kernels run
 // several roles' code at once and are bound by the instruction cache).
+// LIMIT: clock64 cycles before the wait gives up (a short limit serves the
+// self-check of the give-up path, id_check_wait).
+template <long long LIMIT = kWaitCycles>
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
                                                    uint32_t abort_flag, uint32_t sleep_ns);
+template <long long LIMIT = kWaitCycles>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t abort_flag,
                                           uint32_t sleep_ns = 64) {
   if (mbar_try(bar, parity)) return true;
-  return mbar_wait_slow(bar, parity, abort_flag, sleep_ns);
+  return mbar_wait_slow<LIMIT>(bar, parity, abort_flag, sleep_ns);
 }
+template <long long LIMIT>
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
                                                    uint32_t abort_flag, uint32_t sleep_ns) {
   const long long t0 = clock64();
@@ -64,7 +69,7 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity
     if (mbar_try(bar, parity)) return true;
     if ((it & 7) == 7) {
       if (ld_volatile_shared(abort_flag)) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > LIMIT) {
         st_volatile_shared(abort_flag, 1);
         return false;
       }
@@ -115,13 +120,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, 
       ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
       "l"(tmap), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
-}
-
-// Prefetch of one box of a tensor map into L2 (no shared memory, no barrier).
-__device__ __forceinline__ void tma_prefetch_2d(uint64_t tmap, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap),
-               "r"(x), "r"(y)
-               : "memory");
 }
 
 // Bulk copy (no tensor map) of `bytes` (a multiple of 16) from 16-byte aligned
