@@ -95,24 +95,12 @@ struct CoopArgs {
   double tol_factor;
 };
 
-// 128-bit read-only load with an L2 cache policy (createpolicy).  With
-// IDSK_CC_L1NA the lines are not allocated in L1, which then keeps the CTA's
-// rows of V (re-read by every step's u and V^T u phases) instead of the
-// stream of A_c.
-#ifndef IDSK_CC_L1NA
-#define IDSK_CC_L1NA 0
-#endif
+// 128-bit read-only load with an L2 cache policy (createpolicy).
 __device__ __forceinline__ float4 ld_f4_hint(const float* p, uint64_t policy) {
   float4 v;
-#if IDSK_CC_L1NA
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p), "l"(policy));
-#else
   asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p), "l"(policy));
-#endif
   return v;
 }
 
