@@ -470,6 +470,25 @@ __global__ void __launch_bounds__(NTH, 1)
     // a fixed order: quantity g (V_t^T u for g = t < s, ||u||^2 for g = s) is
     // summed by the 8 threads 8 g .. 8 g + 7, thread j over the CTAs b = j
     // mod 8 (all its loads in flight), then a 3-level shuffle tree
+    // The loads that do not depend on the sums go first: u_s (thread 0) and
+    // v_t[s] (thread t < s; s < CT).
+    const float2 us = tid == 0 ? a.V[(int64_t)s * mc + s] : make_float2(0.f, 0.f);
+    const float2 vts = tid < s ? a.V[(int64_t)tid * mc + s] : make_float2(0.f, 0.f);
+    // and the inputs of this warp's first column of phase C: the CTAs'
+    // partials of (A^T u)_j and F(j, 0:s)
+    const int jc = c0 + warp;
+    float2 gv0[8];   // G <= 256
+    double fv0[2];   // s <= 64
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int bb = lane + 32 * e;
+      gv0[e] = (jc < c1 && bb < G) ? pairs[(int64_t)bb * n + jc] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int t = lane + 32 * e;
+      fv0[e] = (jc < c1 && t < s) ? a.F[(int64_t)t * a.ldf + jc] : 0.0;
+    }
     {
       const int g = tid >> 3, j = tid & 7;
       const int q = g < s ? g : (g == s ? kLMax : -1);
@@ -496,7 +515,7 @@ __global__ void __launch_bounds__(NTH, 1)
     cons_sync();
     if (tid == 0) {
       const double sigma = hs[kLMax];
-      const double alpha = df_val(a.V[(int64_t)s * mc + s]);
+      const double alpha = df_val(us);
       double beta = alpha, tau = 0.0, den = 0.0;
       if (sigma != 0.0) {
         const double nrm = sqrt(alpha * alpha + sigma);
@@ -521,13 +540,10 @@ __global__ void __launch_bounds__(NTH, 1)
       }
     }
     cons_sync();
-    {
-      const double rden = rden_sh;
-      for (int t = tid; t < s; t += CT) {
-        const double vst = df_val(a.V[(int64_t)t * mc + s]);   // v_t[s]
-        hvec[t] = vst + hs[t] * rden;
-        vrow[t] = vst;
-      }
+    if (tid < s) {
+      const double vst = df_val(vts);   // v_t[s], t = tid
+      hvec[tid] = vst + hs[tid] * rden_sh;
+      vrow[tid] = vst;
     }
     cons_sync();
     // ---------------------------------------------------------- phase C
@@ -538,15 +554,22 @@ __global__ void __launch_bounds__(NTH, 1)
       for (int j = c0 + warp; j < c1; j += CW) {
         float2 gv[8];   // every load of the lane in flight (G <= 256, s <= 64)
         double fv[2];
+        if (j == jc) {   // loaded at the start of phase B
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int bb = lane + 32 * e;
-          gv[e] = bb < G ? pairs[(int64_t)bb * n + j] : make_float2(0.f, 0.f);
-        }
+          for (int e = 0; e < 8; ++e) gv[e] = gv0[e];
+          fv[0] = fv0[0];
+          fv[1] = fv0[1];
+        } else {
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int t = lane + 32 * e;
-          fv[e] = t < s ? a.F[(int64_t)t * a.ldf + j] : 0.0;
+          for (int e = 0; e < 8; ++e) {
+            const int bb = lane + 32 * e;
+            gv[e] = bb < G ? pairs[(int64_t)bb * n + j] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int t = lane + 32 * e;
+            fv[e] = t < s ? a.F[(int64_t)t * a.ldf + j] : 0.0;
+          }
         }
         // (A^T u)_j: the CTAs' FP32-pair partials summed as FP32 pairs (lane
         // order, then a fixed shuffle tree), one FP64 value at the end
