@@ -566,6 +566,30 @@ def run_batched(args):
                      "ms_per_launch_by_candidate": {str(k): v for k, v in tune_ms.items()}},
         "k_out_short": sum(1 for (_, _, ko), p in zip(res, spec) if ko < p["k"]),
     }
+    # Equal-error comparison (outside the timed region): each problem sketched
+    # in the BF16 form against the plain FP32-accurate form of the same matrix
+    # and the same Psi, both errors from the library's error pass.
+    from paper_1905_13257_gb300 import IdSketch
+    ratios = []
+    for (J, P, ko), p in zip(res, probs):
+        if p["prec"] != "bf16":
+            continue
+        A = p["A"]
+        sk = IdSketch(A.shape[0], A.shape[1], p["k"], p["l"], seed=p["seed"],
+                      dtype=torch.float32, stream=stream)
+        sk.stream_columns(A)
+        J0, P0, k0 = sk.factor()
+        e_plain, _ = sk.reconstruct_error(A, J0[:k0], P0[:k0])
+        e_bf16, _ = sk.reconstruct_error(A, J[:ko], P[:ko])
+        ratios.append(e_bf16 / e_plain)
+        sk.close()
+    if ratios:
+        r = sorted(ratios)
+        line["equal_error"] = {
+            "what": "relative Frobenius error of the batch's BF16-sketch ID / that of the "
+                    "FP32-accurate-sketch ID of the same matrix (same Psi)",
+            "problems": len(r), "min": r[0], "median": r[len(r) // 2], "max": r[-1],
+            "within_1.05": sum(1 for x in r if x <= 1.05)}
     print(json.dumps(line))
     bt.close()
     return 0

@@ -253,6 +253,36 @@ def test_coarse_rank_deficient():
     sk.close()
 
 
+def test_coarse_rank_deficient_fp32_cooperative():
+    """FP32 data on the cooperative coarse QR (m_c a multiple of 4): six
+    independent columns and the rest exactly zero.  The zero columns' norms
+    stay exactly zero, so the rank tolerance stops both the kernel and the
+    oracle after the six (Algorithm 5 with fewer than k pivots)."""
+    grid, nc, n, r, k = (8, 8, 8), 3, 40, 6, 10
+    m = nc * grid[0] * grid[1] * grid[2]
+    g = np.random.default_rng(11)
+    An = np.zeros((m, n))
+    cols = g.choice(n, size=r, replace=False)
+    An[:, cols] = g.normal(size=(m, r))
+    A = torch.tensor(An, dtype=torch.float32).T.contiguous().T.to(DEV)
+    An = A.cpu().double().numpy()
+    sk = _sk(m=m, n_max=n, k=k, l=16, seed=1, dtype=torch.float32, grid=grid, ncomp=nc,
+             coarse_stride=(1, 1, 1), want_coarse=True)
+    sk.stream_columns(A)
+    Jc, Pc, kout = sk.coarse_factor()
+    Jo, Po, ko, margin = oracle.column_id(An, k)
+    assert ko == r and kout == r
+    assert sorted(Jc.cpu().tolist()[:kout]) == sorted(cols.tolist())
+    if margin >= MARGIN:
+        assert Jc.cpu().tolist()[:kout] == Jo.tolist()
+    P = Pc.cpu().numpy()[:kout]
+    assert_valid_skeleton(Jc.cpu().numpy()[:kout], P, kout, n)
+    zero = np.setdiff1d(np.arange(n), cols)
+    assert np.all(P[:, zero] == 0.0)
+    assert all(j == -1 for j in Jc.cpu().tolist()[kout:])
+    sk.close()
+
+
 # ------------------------------------------------------------- error pass
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
