@@ -485,15 +485,15 @@ def run_ours(args):
 def batched_problems(count=64, seed=1):
     """Sizes of the batched workload: 64 channel fields of uneven size, m ~
     U[50k, 2M] rounded to 3 nx ny nz with nx = nz = 2 ny, n ~ U[64, 512],
-    k ~ U[10, 54] (l = k + 10 <= 64, the library's sketch width), seeds 1..64,
-    FP32 data, every other problem in the BF16 sketch form."""
+    k ~ U[10, 80], l = k + 10 (above 64, W in two passes of Psi rows), seeds
+    1..64, FP32 data, every other problem in the BF16 sketch form."""
     import numpy as np
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
         ny = max(2, int(round((rng.uniform(50_000, 2_000_000) / 12.0) ** (1.0 / 3.0))))
         n = int(rng.integers(64, 513))
-        k = int(rng.integers(10, 55))
+        k = int(rng.integers(10, 81))
         out.append(dict(grid=(2 * ny, ny, 2 * ny), n=n, k=k, l=k + 10, seed=b + 1,
                         prec="bf16" if b % 2 else "exact"))
     return out
@@ -551,7 +551,7 @@ def run_batched(args):
         "data": "synthetic channel fields (seeded), resident in HBM",
         "config": {"workload": "64 channel fields of uneven size in one graph launch: "
                                "m ~ U[50k, 2M] (3 x 2ny x ny x 2ny), n ~ U[64, 512], "
-                               "k ~ U[10, 54], l = k + 10, seeds 1..64, FP32, "
+                               "k ~ U[10, 80], l = k + 10, seeds 1..64, FP32, "
                                "every other problem BF16 sketch",
                    "problems": len(probs), "bytes_per_step": nbytes,
                    "m_range": [min(ms_), max(ms_)],
@@ -568,15 +568,15 @@ def run_batched(args):
     }
     # Equal-error comparison (outside the timed region): each problem sketched
     # in the BF16 form against the plain FP32-accurate form of the same matrix
-    # and the same Psi, both errors from the library's error pass.
+    # and the same Psi, both errors from the library's error pass (k <= 64).
     from paper_1905_13257_gb300 import IdSketch
     ratios = []
     for (J, P, ko), p in zip(res, probs):
-        if p["prec"] != "bf16":
+        if p["prec"] != "bf16" or p["k"] > 64:
             continue
         A = p["A"]
         sk = IdSketch(A.shape[0], A.shape[1], p["k"], p["l"], seed=p["seed"],
-                      dtype=torch.float32, stream=stream)
+                      dtype=torch.float32, want_Y=False, stream=stream)
         sk.stream_columns(A)
         J0, P0, k0 = sk.factor()
         e_plain, _ = sk.reconstruct_error(A, J0[:k0], P0[:k0])
@@ -587,7 +587,8 @@ def run_batched(args):
         r = sorted(ratios)
         line["equal_error"] = {
             "what": "relative Frobenius error of the batch's BF16-sketch ID / that of the "
-                    "FP32-accurate-sketch ID of the same matrix (same Psi)",
+                    "FP32-accurate-sketch ID of the same matrix (same Psi); the BF16 "
+                    "problems with k <= 64 (the error pass's limit)",
             "problems": len(r), "min": r[0], "median": r[len(r) // 2], "max": r[-1],
             "within_1.05": sum(1 for x in r if x <= 1.05)}
     print(json.dumps(line))

@@ -68,7 +68,8 @@ typedef struct {
   int64_t m;               /* rows of A = ncomp * nx * ny * nz (or any m > 0)  */
   int64_t n_max;           /* column capacity: total columns streamed <= n_max */
   int32_t k;               /* target rank, 1 <= k <= l                          */
-  int32_t l;               /* sketch width l = k + p, l <= 64                   */
+  int32_t l;               /* sketch width l = k + p, l <= 64; up to 96 for FP32
+                              data without Y (see id_sketch_create)             */
   uint64_t seed;           /* seed of Psi and Omega (Philox4x32-10 key)         */
   int32_t dtype;           /* id_dtype of the streamed columns                  */
   int32_t prec;            /* id_sketch_prec                                    */
@@ -89,9 +90,17 @@ typedef struct id_sketch id_sketch;   /* opaque, library-owned */
  * FP64), Y (m x l, dtype) and A_c (m_c x n_max, dtype) as requested.
  * Passage: Algorithm 4 steps 2-3 (Gaussian Omega, l = k + p; Sec. 2.2).
  * cuda_stream may be NULL (legacy default stream).
+ * Sketch width: l <= 64 for every form.  FP32 data without Y may take
+ * 64 < l <= 96 (k up to 86 at p = 10): the tensor-core sketch then forms W in
+ * passes of 60 rows of Psi over each window (one more read of the window per
+ * pass), the pivoted QR and the solve take the wider W, and the coarse-grid
+ * QR, the error pass and the single-pass ID keep k <= 64.
  * Errors: ID_ERR_INVALID_ARG for an inconsistent config (m <= 0, n_max <= 0,
- * k < 1, k > l, l > 64, grid/ncomp not matching m when want_coarse, a coarse
- * stride < 1, reserved fields != 0), ID_ERR_OOM, ID_ERR_CUDA. */
+ * k < 1, k > l, l > 96, grid/ncomp not matching m when want_coarse, a coarse
+ * stride < 1, reserved fields != 0), ID_ERR_UNSUPPORTED (l > 64 with FP64
+ * data or want_Y; k > 64 with want_coarse; at id_sketch_stream_columns, l > 64
+ * with columns that the tensor-core sketch cannot read: m < 128 or columns
+ * not 16-byte aligned), ID_ERR_OOM, ID_ERR_CUDA. */
 id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** out);
 
 /* Stream ncols snapshot columns (device pointer, column-major, leading
@@ -241,7 +250,7 @@ typedef struct {
   int64_t m;         /* rows, >= 1                                            */
   int32_t n;         /* snapshots, 1 <= n <= ID_BATCH_MAX_COLS                */
   int32_t k;         /* target rank, 1 <= k <= min(l, n)                      */
-  int32_t l;         /* sketch width, k <= l <= 64                            */
+  int32_t l;         /* sketch width, k <= l <= 64 (<= 96 for FP32 data)     */
   int32_t dtype;     /* id_dtype of A                                         */
   int32_t prec;      /* id_sketch_prec (ID_SKETCH_BF16 for FP32 data only)    */
   int32_t reserved;  /* must be zero                                          */

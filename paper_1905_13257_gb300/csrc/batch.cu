@@ -64,7 +64,8 @@ id_status fail_cuda(id_batch* b, cudaError_t e) {
 id_status check_problem(const id_batch_problem& p) {
   if (!p.d_A || p.m < 1 || p.lda < p.m || p.n < 1 || p.n > ID_BATCH_MAX_COLS)
     return ID_ERR_INVALID_ARG;
-  if (p.k < 1 || p.l < p.k || p.l > kLMax || p.k > p.n) return ID_ERR_INVALID_ARG;
+  if (p.k < 1 || p.l < p.k || p.l > kLMaxW || p.k > p.n) return ID_ERR_INVALID_ARG;
+  if (p.l > kLMax && p.dtype != ID_F32) return ID_ERR_INVALID_ARG;
   if (p.dtype != ID_F32 && p.dtype != ID_F64) return ID_ERR_INVALID_ARG;
   if (p.prec != ID_SKETCH_EXACT && p.prec != ID_SKETCH_BF16) return ID_ERR_INVALID_ARG;
   if (p.prec == ID_SKETCH_BF16 && p.dtype != ID_F32) return ID_ERR_INVALID_ARG;

@@ -99,7 +99,11 @@ void free_all(id_sketch* h) {
 id_status validate(const id_config* c) {
   if (!c) return ID_ERR_INVALID_ARG;
   if (c->m <= 0 || c->n_max <= 0 || c->n_max > (int64_t)1 << 30) return ID_ERR_INVALID_ARG;
-  if (c->k < 1 || c->l < c->k || c->l > kLMax) return ID_ERR_INVALID_ARG;
+  if (c->k < 1 || c->l < c->k || c->l > kLMaxW) return ID_ERR_INVALID_ARG;
+  // l > 64: FP32 data, W only (the tensor-core sketch in passes; no Y), and
+  // no coarse-grid QR above k = 64
+  if (c->l > kLMax && (c->dtype != ID_F32 || c->want_Y)) return ID_ERR_UNSUPPORTED;
+  if (c->want_coarse && c->k > kLMax) return ID_ERR_UNSUPPORTED;
   if (c->dtype != ID_F32 && c->dtype != ID_F64) return ID_ERR_INVALID_ARG;
   if (c->prec != ID_SKETCH_EXACT && c->prec != ID_SKETCH_BF16) return ID_ERR_INVALID_ARG;
   if (c->prec == ID_SKETCH_BF16 && c->dtype != ID_F32) return ID_ERR_INVALID_ARG;
@@ -148,6 +152,7 @@ id_status launch_pending(id_sketch* h) {
     memset(&w, 0, sizeof(w));
     w.col_base = h->n_launched;
     const bool tc = use_tc(h);
+    if (!tc && h->l > kLMax) return ID_ERR_UNSUPPORTED;   // wide sketches: tensor-core path only
     const int wmax = tc ? kTcMaxTiles * 128 : kSimtWindowMax;
     int taken = 0;
     size_t consumed = 0;

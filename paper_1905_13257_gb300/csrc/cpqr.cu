@@ -16,9 +16,9 @@
 // step, each CTA's best candidate and then the pivot column are published in
 // its shared memory and read by the other CTAs through distributed shared
 // memory (two cluster barriers per step, double-buffered slots).
-// Larger n (cpqr_small_kernel): one CTA of 1024 threads works in place on a
-// copy of W held row-major in global memory (L2-resident); thread t owns
-// columns t, t + 1024, ...
+// Larger n, or l > 64 rows (cpqr_small_kernel, up to 96 rows): one CTA of 1024
+// threads works in place on a copy of W held row-major in global memory
+// (L2-resident); thread t owns columns t, t + 1024, ...
 // In both, norms and the argmax use warp shuffles and fixed-order sums, and
 // the reflector of the pivot column is formed by one warp.
 #include <cooperative_groups.h>
@@ -66,7 +66,7 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
                   double* __restrict__ R, int* __restrict__ J, int* __restrict__ colpos,
                   int* __restrict__ kout) {
   __shared__ ArgMax red[NT / 32];
-  __shared__ double vs[kLMax];
+  __shared__ double vs[kLMaxW];
   __shared__ double sh_tau, sh_beta, sh_tol;
   __shared__ int sh_p, sh_stop;
   __shared__ double fro_part[NT / 32];
@@ -127,13 +127,15 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
     __syncthreads();
     if (sh_stop) break;
     const int p = sh_p;
-    // Householder reflector of the pivot column, rows s..rows-1 (one warp)
+    // Householder reflector of the pivot column, rows s..rows-1 (one warp;
+    // lane holds rows s + lane, s + lane + 32, s + lane + 64)
     if (warp == 0) {
       const int len = rows - s;
       double x0 = (lane < len) ? M[(int64_t)(s + lane) * ld + p] : 0.0;
       double x1 = (lane + 32 < len) ? M[(int64_t)(s + lane + 32) * ld + p] : 0.0;
+      double x2 = (lane + 64 < len) ? M[(int64_t)(s + lane + 64) * ld + p] : 0.0;
       const double alpha = __shfl_sync(0xffffffffu, x0, 0);
-      const double sigma = warp_sum((lane == 0 ? 0.0 : x0 * x0) + x1 * x1);
+      const double sigma = warp_sum((lane == 0 ? 0.0 : x0 * x0) + x1 * x1 + x2 * x2);
       double tau = 0.0, beta = alpha, scale = 0.0;
       if (sigma != 0.0) {
         const double nrm = sqrt(alpha * alpha + sigma);
@@ -143,6 +145,7 @@ cpqr_small_kernel(double* __restrict__ M, int rows, int n, int ld, int k, double
       }
       if (lane < len) vs[lane] = lane == 0 ? 1.0 : (sigma != 0.0 ? x0 / scale : 0.0);
       if (lane + 32 < len) vs[lane + 32] = sigma != 0.0 ? x1 / scale : 0.0;
+      if (lane + 64 < len) vs[lane + 64] = sigma != 0.0 ? x2 / scale : 0.0;
       if (lane == 0) {
         sh_tau = tau;
         sh_beta = beta;
@@ -322,8 +325,8 @@ __global__ void __launch_bounds__(SP_WARPS * 32) solve_p_kernel(
     const double* __restrict__ R, const int* __restrict__ J, const int* __restrict__ colpos,
     const int* __restrict__ kout, int k, int n, double* __restrict__ P) {
   extern __shared__ double r11[];   // kk x kk, row-major
-  __shared__ int Js[kLMax];
-  __shared__ double rdiag[kLMax];   // 1 / R11(t, t)
+  __shared__ int Js[kLMaxW];
+  __shared__ double rdiag[kLMaxW];   // 1 / R11(t, t)
   const int kk = *kout;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) Js[e] = J[e];
   __syncthreads();
@@ -342,31 +345,36 @@ __global__ void __launch_bounds__(SP_WARPS * 32) solve_p_kernel(
     for (int tt = lane; tt < k; tt += 32) P[(int64_t)tt * n + j] = (tt == cp) ? 1.0 : 0.0;
     return;
   }
+  // lane u holds b_u, b_{u+32}, b_{u+64} (k_out <= 96)
   double b0 = lane < kk ? R[(int64_t)lane * n + j] : 0.0;
   double b1 = lane + 32 < kk ? R[(int64_t)(lane + 32) * n + j] : 0.0;
+  double b2 = lane + 64 < kk ? R[(int64_t)(lane + 64) * n + j] : 0.0;
   for (int tt = kk - 1; tt >= 0; --tt) {
-    const double bt = __shfl_sync(0xffffffffu, tt < 32 ? b0 : b1, tt & 31);
+    const double bt = __shfl_sync(0xffffffffu, tt < 32 ? b0 : (tt < 64 ? b1 : b2), tt & 31);
     const double xt = bt * rdiag[tt];
     if (lane == (tt & 31)) {
       if (tt < 32)
         b0 = xt;
-      else
+      else if (tt < 64)
         b1 = xt;
+      else
+        b2 = xt;
     }
     if (lane < tt) b0 -= r11[lane * kk + tt] * xt;
     if (lane + 32 < tt) b1 -= r11[(lane + 32) * kk + tt] * xt;
+    if (lane + 64 < tt) b2 -= r11[(lane + 64) * kk + tt] * xt;
   }
-  // lane tt & 31 holds x_tt (in b0 for tt < 32, in b1 otherwise); rows past k_out are 0
+  // lane tt & 31 holds x_tt (in b0, b1 or b2 by tt / 32); rows past k_out are 0
   for (int tt = lane; tt < k; tt += 32)
-    P[(int64_t)tt * n + j] = tt < kk ? (tt < 32 ? b0 : b1) : 0.0;
+    P[(int64_t)tt * n + j] = tt < kk ? (tt < 32 ? b0 : (tt < 64 ? b1 : b2)) : 0.0;
 }
 
 }  // namespace
 
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
                               double* R, int* J, int* colpos, int* kout, cudaStream_t st) {
-  if (n > NT * QMAX || rows > kLMax) return cudaErrorInvalidValue;
-  if (n <= CL_CTAS * CL_THREADS)
+  if (n > NT * QMAX || rows > kLMaxW || k > kLMaxW) return cudaErrorInvalidValue;
+  if (n <= CL_CTAS * CL_THREADS && rows <= kLMax)   // the cluster kernel: a column in registers
     cpqr_cluster_kernel<<<CL_CTAS, CL_THREADS, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J,
                                                         colpos, kout);
   else

@@ -13,6 +13,12 @@ namespace idsk {
 
 // ------------------------------------------------------------------ limits
 constexpr int kLMax = 64;             // sketch width l (padded to 16 on device)
+// Wider sketches, l <= kLMaxW (so k <= 86 at l = k + 10): FP32 data on the
+// tensor-core sketch without Y, in passes of at most kPassRows rows of Psi
+// (one more read of each window per pass); the one-CTA pivoted QR and the
+// solve take up to kLMaxW rows and pivots.  Everything else keeps k, l <= 64.
+constexpr int kLMaxW = 96;
+constexpr int kPassRows = 60;         // a multiple of 10: Psi's counter blocks
 constexpr int kMaxSegs = 64;          // column segments per sketch launch
 constexpr int kSimtWindowMax = 320;   // columns per SIMT sketch launch
 constexpr int kTcMaxTiles = 4;        // 128-column tiles per tensor-core launch (TMEM budget)
@@ -105,6 +111,7 @@ struct SketchArgs {
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
   float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][64]
+  int32_t s0;           // first row of Psi drawn by this launch (a multiple of 10)
 };
 
 // ------------------------------------------------ single-pass ID (Alg. 6)

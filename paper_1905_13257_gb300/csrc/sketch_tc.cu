@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       for (int sb = 0; sb * 10 < LP; ++sb) {
         float g[10];
         if (r < a.m) {
-          gauss10((uint64_t)r, (uint32_t)sb, kStreamPsi, a.k0, a.k1, a.table, g);
+          gauss10((uint64_t)r, (uint32_t)(sb + a.s0 / 10), kStreamPsi, a.k0, a.k1, a.table, g);
         } else {
 #pragma unroll
           for (int f = 0; f < 10; ++f) g[f] = 0.f;
@@ -768,10 +768,28 @@ extern "C" int idsk_tc_trace_read(long long* host) {
 }
 #endif
 
-cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
+cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces, int nsm,
                              int drain_blocks, int* status, cudaStream_t st, KernelTimer* timer) {
   if (w.ncols <= 0) return cudaSuccess;
-  if (w.ncols > kTcMaxTiles * TCOLS || a.l > LP) return cudaErrorInvalidValue;
+  if (w.ncols > kTcMaxTiles * TCOLS || a0.l > kLMaxW || a0.s0 % 10 != 0)
+    return cudaErrorInvalidValue;
+  if (a0.l > LP) {
+    if (a0.s0 != 0) return cudaErrorInvalidValue;
+    // a wide sketch (W only): one launch per kPassRows rows of Psi, the
+    // coarse rows gathered by the first
+    if (a0.want_Y) return cudaErrorInvalidValue;
+    for (int s0 = 0; s0 < a0.l; s0 += kPassRows) {
+      SketchArgs a = a0;
+      a.s0 = s0;
+      a.l = std::min(kPassRows, a0.l - s0);
+      a.W = a0.W + (int64_t)s0 * a0.ldw;
+      if (s0 > 0) a.cg.on = 0;
+      const cudaError_t e = launch_sketch_tc(a, w, npieces, nsm, drain_blocks, status, st, timer);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  const SketchArgs& a = a0;
   const int64_t nrb = (a.m + TR - 1) / TR;
   const int grid = (int)std::min<int64_t>(nrb, nsm);
   CUtensorMap tm;

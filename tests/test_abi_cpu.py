@@ -67,7 +67,7 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(m=0), dict(n_max=0), dict(k=0), dict(k=9, l=8),
-                                 dict(l=65, k=4), dict(dtype=3), dict(prec=7),
+                                 dict(l=97, k=4), dict(dtype=3), dict(prec=7),
                                  dict(prec=1, dtype=1), dict(window_cols=-1),
                                  dict(want_coarse=1, ncomp=3, grid=(10, 10, 10),
                                       coarse_stride=(2, 2, 2)),  # 3000 != m
@@ -78,6 +78,18 @@ def test_invalid_config_rejected_before_any_gpu_call(lib, bad):
     h = C.c_void_p(123)
     cfg = _cfg(**bad)
     assert lib.id_sketch_create(C.byref(cfg), None, C.byref(h)) == 1
+    assert h.value is None
+
+
+@pytest.mark.parametrize("bad", [dict(l=65, k=4, want_Y=1), dict(l=90, k=80, dtype=1),
+                                 dict(want_coarse=1, ncomp=1, grid=(10, 10, 10),
+                                      coarse_stride=(1, 1, 1), k=65, l=70)])
+def test_wide_sketch_limits_rejected_before_any_gpu_call(lib, bad):
+    """l > 64 serves FP32 data without Y, and the coarse QR keeps k <= 64:
+    the other requests are unsupported (not invalid), before any GPU call."""
+    h = C.c_void_p(123)
+    cfg = _cfg(**bad)
+    assert lib.id_sketch_create(C.byref(cfg), None, C.byref(h)) == 7
     assert h.value is None
 
 
@@ -105,7 +117,8 @@ def _prob(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(d_A=None), dict(m=0), dict(lda=999), dict(n=0),
-                                 dict(n=513), dict(k=0), dict(k=9, l=8), dict(l=65),
+                                 dict(n=513), dict(k=0), dict(k=9, l=8), dict(l=97),
+                                 dict(l=65, dtype=1),
                                  dict(k=65, l=64, n=64),
                                  dict(dtype=2), dict(prec=2), dict(prec=1, dtype=1),
                                  dict(reserved=1)])

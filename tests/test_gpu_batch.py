@@ -31,6 +31,8 @@ CASES = [
     ((16, 8, 16), 300, 16, 26, torch.float64, "exact"),  # FP64 data (SIMT sketch)
     ((8, 4, 8), 64, 10, 64, torch.float64, "exact"),     # l at the limit
     ((24, 12, 24), 130, 24, 34, torch.float32, "exact"),  # m = 20,736
+    ((16, 8, 16), 200, 70, 80, torch.float32, "exact"),   # wide sketch: two Psi passes
+    ((20, 10, 20), 300, 80, 90, torch.float32, "bf16"),   # wide, BF16 form, k = 80
 ]
 
 

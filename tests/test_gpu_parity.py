@@ -153,6 +153,37 @@ def test_factor_parity_gap_input(dtype, grid, n, k, l):
     sk.close()
 
 
+@pytest.mark.parametrize("prec", ["exact", "bf16"])
+def test_wide_sketch_factor(prec):
+    """l = 90, k = 80 (FP32 data, W only): the sketch in two passes of Psi
+    rows (0-59, 60-89), the one-CTA pivoted QR of the 90-row W and the solve
+    for 80 pivots, against the oracle on the same Psi."""
+    grid, n, k, l = (16, 12, 16), 240, 80, 90
+    A = channel_field(grid, 3, n, seed=7, gap_k=k, dtype=torch.float32, device=DEV)
+    m = A.shape[0]
+    An = (A.to(torch.bfloat16) if prec == "bf16" else A).double().cpu().numpy()
+    seed, Wo, (Jo, Po, ko, margin) = sketch_seed_with_margin(An, k, l, range(9, 41))
+    sk = _sk(m=m, n_max=n, k=k, l=l, seed=seed, dtype=torch.float32, want_Y=False, prec=prec)
+    stream(sk, A, [32] * (n // 32) + ([n % 32] if n % 32 else []))
+    W = sk.sketches()[0].cpu().numpy()
+    assert rel(W, Wo) <= 1e-5
+    J, P, kout = sk.factor()
+    assert kout == ko == k
+    Pg, Jg = P.cpu().numpy(), J.cpu().numpy()
+    assert_valid_skeleton(Jg, Pg, k, n)
+    Jw, Pw, _, mw = oracle.column_id(W, k)      # same W: FP64 QR agreement
+    if mw >= MARGIN:
+        assert Jg.tolist() == Jw.tolist()
+        assert np.max(np.abs(Pg - Pw)) <= 1e-9 * max(1.0, np.max(np.abs(Pw)))
+    if margin >= MARGIN:
+        assert Jg.tolist() == Jo.tolist()
+    else:
+        fo, _ = oracle.recon_error(An, Jo, Po)
+        fg, _ = oracle.recon_error(An, Jg, Pg)
+        assert fg <= 1.05 * fo
+    sk.close()
+
+
 def test_factor_host_outputs_and_edge_ranks():
     A = channel_field((8, 8, 8), 3, 40, seed=2, gap_k=8, dtype=torch.float64, device=DEV)
     m = A.shape[0]
