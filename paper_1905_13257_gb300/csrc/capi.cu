@@ -146,7 +146,22 @@ bool use_tc(const id_sketch* h) {
 
 namespace idsk {
 
+// Orders the side stream's coarse QR (if any is in flight) before the work
+// that id_sketch's own stream enqueues next: it reads A_c and writes the
+// coarse workspace, which a new sketch or a reset would overwrite.
+id_status join_coarse(id_sketch* h) {
+  if (!h->cq_pending) return ID_OK;
+  IDSK_CUDA(h, cudaStreamWaitEvent(h->st, h->ev_cq, 0));
+  h->cq_pending = false;
+  return ID_OK;
+}
+
 id_status launch_pending(id_sketch* h) {
+  if (!h->pend.empty()) {
+    const id_status s = join_coarse(h);
+    if (s != ID_OK) return s;
+    h->coarse_spec = -1;   // new columns: a started coarse QR no longer applies
+  }
   while (!h->pend.empty()) {
     Window w;
     memset(&w, 0, sizeof(w));
@@ -206,7 +221,7 @@ id_status launch_pending(id_sketch* h) {
   return ID_OK;
 }
 
-id_status factor_enqueue(id_sketch* h) {
+id_status factor_enqueue(id_sketch* h, bool one_cta) {
   id_status s = launch_pending(h);
   if (s != ID_OK) return s;
   const int64_t n = h->n_seen;
@@ -216,10 +231,11 @@ id_status factor_enqueue(id_sketch* h) {
                                  sizeof(double) * h->n_max, sizeof(double) * n, l,
                                  cudaMemcpyDeviceToDevice, h->st));
   IDSK_CUDA(h, launch_cpqr_small(h->d_work, l, (int)n, (int)n, k, ID_RANK_TOL_FACTOR, h->d_R,
-                                 h->d_J, h->d_colpos, h->d_kout, h->st));
+                                 h->d_J, h->d_colpos, h->d_kout, h->st, one_cta));
   IDSK_CUDA(h, launch_solve_p(h->d_R, h->d_J, h->d_colpos, h->d_kout, k, (int)n, h->d_P, h->st));
   return ID_OK;
 }
+
 
 }  // namespace idsk
 
@@ -411,7 +427,16 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_W, 0, sizeof(double) * l * nm, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess && cfg->want_coarse && cfg->dtype == ID_F32 &&
+      !getenv("IDSKETCH_NO_SIDE_STREAM")) {
+    e = cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sk, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_cq, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
+    if (h->st2) cudaStreamDestroy(h->st2);
+    if (h->ev_sk) cudaEventDestroy(h->ev_sk);
+    if (h->ev_cq) cudaEventDestroy(h->ev_cq);
     free_all(h);
     delete h;
     return ID_ERR_CUDA;
@@ -457,6 +482,9 @@ id_status id_sketch_flush(id_sketch* h) {
 id_status id_sketch_reset(id_sketch* h) {
   if (!h) return ID_ERR_INVALID_ARG;
   if (h->poisoned) return ID_ERR_CUDA;
+  const id_status js = join_coarse(h);
+  if (js != ID_OK) return js;
+  h->coarse_spec = -1;
   h->pend.clear();
   h->pend_cols = 0;
   h->n_seen = 0;
@@ -469,8 +497,26 @@ id_status id_sketch_reset(id_sketch* h) {
 id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out) {
   if (!h) return ID_ERR_INVALID_ARG;
   if (h->poisoned) return ID_ERR_CUDA;
-  id_status s = factor_enqueue(h);
+  id_status s = launch_pending(h);
   if (s != ID_OK) return s;
+  if (h->n_seen == 0) return ID_ERR_STATE;
+  // With want_coarse, the coarse QR of these columns (Algorithm 5) starts now
+  // on the side stream, on all SMs but one, and the QR of W runs beside it in
+  // one CTA; id_coarse_factor then only waits for it.
+  const bool spec = h->st2 && h->coarse_spec != h->n_seen &&
+                    coarse_coop_ok_ctas(h, h->nsm - 1);
+  if (spec) IDSK_CUDA(h, cudaEventRecord(h->ev_sk, h->st));
+  s = factor_enqueue(h, spec);
+  if (s != ID_OK) return s;
+  if (spec) {
+    const id_status js = join_coarse(h);   // an earlier coarse QR, if any
+    if (js != ID_OK) return js;
+    IDSK_CUDA(h, cudaStreamWaitEvent(h->st2, h->ev_sk, 0));
+    IDSK_CUDA(h, launch_coarse_coop(h, h->n_seen, h->st2, h->nsm - 1));
+    IDSK_CUDA(h, cudaEventRecord(h->ev_cq, h->st2));
+    h->coarse_spec = h->n_seen;
+    h->cq_pending = true;
+  }
   const int64_t n = h->n_seen;
   const int k = h->k;
   if ((s = copy_out(h, J, h->d_J, sizeof(int32_t) * k)) != ID_OK) return s;
@@ -540,7 +586,13 @@ id_status id_coarse_factor(id_sketch* h, int32_t* Jc, double* Pc, int32_t* k_out
   const int64_t n = h->n_seen;
   if (n == 0) return ID_ERR_STATE;
   const int k = h->k;
-  IDSK_CUDA(h, launch_coarse_cpqr(h, n, h->st));
+  if (h->coarse_spec == n) {   // started by id_factor on the side stream
+    if ((s = join_coarse(h)) != ID_OK) return s;
+  } else {
+    if ((s = join_coarse(h)) != ID_OK) return s;
+    IDSK_CUDA(h, launch_coarse_cpqr(h, n, h->st));
+    h->coarse_spec = -1;
+  }
   if ((s = copy_out(h, Jc, h->d_Jc, sizeof(int32_t) * k)) != ID_OK) return s;
   if ((s = copy_out(h, Pc, h->d_Pc, sizeof(double) * k * n)) != ID_OK) return s;
   int32_t kk = 0, dst = 0;
@@ -743,6 +795,12 @@ id_status id_check_wait(int32_t device, int32_t mode) {
 void id_sketch_destroy(id_sketch* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  if (h->st2) {
+    cudaStreamSynchronize(h->st2);
+    cudaStreamDestroy(h->st2);
+  }
+  if (h->ev_sk) cudaEventDestroy(h->ev_sk);
+  if (h->ev_cq) cudaEventDestroy(h->ev_cq);
   free_all(h);
   delete h->timer_sketch;
   delete h->timer_recon;

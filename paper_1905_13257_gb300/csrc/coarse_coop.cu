@@ -716,7 +716,10 @@ extern "C" int idsk_cc_trace_read(long long* host) {
 
 // Whether the cooperative form serves this handle: FP32 A_c with m_c a
 // multiple of 4 (16-byte row quads) and at most 512 rows per CTA.
-bool coarse_coop_ok(const id_sketch* h) {
+bool coarse_coop_ok(const id_sketch* h) { return coarse_coop_ok_ctas(h, 0); }
+
+// The same with at most max_ctas CTAs (0: one per SM).
+bool coarse_coop_ok_ctas(const id_sketch* h, int max_ctas) {
   if (h->cfg.dtype != ID_F32 || (h->mc & 3) != 0 || getenv("IDSKETCH_COARSE_MULTI")) return false;
   int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev) != cudaSuccess ||
@@ -725,8 +728,9 @@ bool coarse_coop_ok(const id_sketch* h) {
     return false;
   }
   const int64_t Q = h->mc / 4;
-  const int64_t G = std::min<int64_t>(h->nsm, Q);
-  return Q >= 1 && G <= 256 && (Q + G - 1) / G <= QMAX && h->coarse_blocks >= G;
+  const int cap = max_ctas > 0 ? std::min(max_ctas, h->nsm) : h->nsm;
+  const int64_t G = std::min<int64_t>(cap, Q);
+  return Q >= 1 && G >= 1 && G <= 256 && (Q + G - 1) / G <= QMAX && h->coarse_blocks >= G;
 }
 
 // Runs one self-check of the bounded waits (modes as id_check_wait) on
@@ -760,10 +764,11 @@ cudaError_t run_wait_check(int mode, cudaStream_t st, int* gave_up) {
   return cudaSuccess;
 }
 
-cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st) {
+cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st, int max_ctas) {
   const int n = (int)n64;
   const int64_t Q = h->mc / 4;
-  const int G = (int)std::min<int64_t>(h->nsm, Q);   // every CTA owns a row quad
+  const int cap = max_ctas > 0 ? std::min(max_ctas, h->nsm) : h->nsm;
+  const int G = (int)std::min<int64_t>(cap, Q);   // every CTA owns a row quad
   CoopArgs a;
   a.Ac = reinterpret_cast<const float*>(h->d_Ac);
   a.mc = h->mc;

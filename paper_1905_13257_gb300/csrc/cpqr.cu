@@ -371,10 +371,13 @@ __global__ void __launch_bounds__(SP_WARPS * 32) solve_p_kernel(
 
 }  // namespace
 
+// one_cta: the one-CTA kernel whatever the size (the QR then occupies a
+// single SM, beside the coarse QR that id_factor starts on a side stream).
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
-                              double* R, int* J, int* colpos, int* kout, cudaStream_t st) {
+                              double* R, int* J, int* colpos, int* kout, cudaStream_t st,
+                              bool one_cta) {
   if (n > NT * QMAX || rows > kLMaxW || k > kLMaxW) return cudaErrorInvalidValue;
-  if (n <= CL_CTAS * CL_THREADS && rows <= kLMax)   // the cluster kernel: a column in registers
+  if (!one_cta && n <= CL_CTAS * CL_THREADS && rows <= kLMax)   // cluster: a column in registers
     cpqr_cluster_kernel<<<CL_CTAS, CL_THREADS, 0, st>>>(M, rows, n, ld, k, tol_factor, R, J,
                                                         colpos, kout);
   else

@@ -263,6 +263,14 @@ struct id_sketch {
   int* d_Jc = nullptr;        // k
   int* d_colposc = nullptr;   // n_max
   int coarse_blocks = 0;
+  // The coarse QR of the same columns started by id_factor on a side stream
+  // (want_coarse, FP32, cooperative form): it runs beside the small QR of W
+  // and id_coarse_factor only waits for it.
+  cudaStream_t st2 = nullptr;     // side stream (created with the handle)
+  cudaEvent_t ev_sk = nullptr;    // the sketch of the columns is complete
+  cudaEvent_t ev_cq = nullptr;    // the side stream's coarse QR is complete
+  int64_t coarse_spec = -1;       // n_seen of the started coarse QR (-1: none)
+  bool cq_pending = false;        // side-stream work not yet ordered before h->st
   // error-pass workspace
   double* d_part = nullptr;   // rec_blocks x 3
   double* d_out3 = nullptr;   // 3
@@ -292,14 +300,16 @@ cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, 
                              int drain_blocks, int* status, cudaStream_t st,
                              KernelTimer* timer = nullptr);
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
-                              double* R, int* J, int* colpos, int* kout, cudaStream_t st);
+                              double* R, int* J, int* colpos, int* kout, cudaStream_t st,
+                              bool one_cta = false);
 cudaError_t launch_solve_p(const double* R, const int* J, const int* colpos, const int* kout,
                            int k, int n, double* P, cudaStream_t st);
 cudaError_t launch_coarse_cpqr(id_sketch* h, int64_t n, cudaStream_t st);
 // The coarse QR as one cooperative launch (coarse_coop.cu): FP32 A_c, m_c a
 // multiple of 4, at most 512 rows per CTA.
 bool coarse_coop_ok(const id_sketch* h);
-cudaError_t launch_coarse_coop(id_sketch* h, int64_t n, cudaStream_t st);
+cudaError_t launch_coarse_coop(id_sketch* h, int64_t n, cudaStream_t st, int max_ctas = 0);
+bool coarse_coop_ok_ctas(const id_sketch* h, int max_ctas);
 cudaError_t run_wait_check(int mode, cudaStream_t st, int* gave_up);
 cudaError_t launch_recon_error(const void* A, int64_t lda, int64_t m, int64_t n, int dtype,
                                const int* J, const double* P, int k, double* part, int nblk,
@@ -333,5 +343,5 @@ id_status launch_pending(id_sketch* h);
 // Enqueue the randomized ID of the streamed columns (pivoted QR of W and the
 // solve for P) into h->d_J, h->d_P, h->d_kout, with no host synchronisation
 // (capi.cu).  ID_ERR_STATE when no column was streamed.
-id_status factor_enqueue(id_sketch* h);
+id_status factor_enqueue(id_sketch* h, bool one_cta = false);
 }  // namespace idsk

@@ -20,7 +20,7 @@ def test_batched_workload_follows_its_rules():
         m = 3 * nx * ny * nz
         assert 40_000 <= m <= 2_100_000                   # U[50k, 2M] rounded to the grid
         assert 64 <= p["n"] <= 512
-        assert 10 <= p["k"] <= 54 and p["l"] == p["k"] + 10 <= 64
+        assert 10 <= p["k"] <= 80 and p["l"] == p["k"] + 10 <= 90
         assert p["prec"] == ("bf16" if b % 2 else "exact")
     # the same sizes on every call (seeded)
     assert bench.batched_problems() == ps
