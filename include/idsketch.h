@@ -137,6 +137,11 @@ id_status id_sketch_reset(id_sketch* h);
  * to the lowest column index.
  * Returns ID_ERR_RANK_DEFICIENT when fewer than k pivots clear the rank
  * tolerance; J and the first k_out rows of P are still valid.
+ * With want_coarse (FP32 data, cooperative coarse QR), the call also starts
+ * id_coarse_factor's QR of the same columns on an internal stream of the
+ * handle, on all SMs but one, and runs the QR of W in one CTA beside it; it
+ * returns when J, P and k_out are ready.  The handle orders that work before
+ * anything that would overwrite its inputs (new columns, a reset).
  * Errors: ID_ERR_STATE when no column was streamed. */
 id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out);
 
@@ -145,6 +150,8 @@ id_status id_factor(id_sketch* h, int32_t* J, double* P, int32_t* k_out);
  * during the pass, then P_c as in id_factor.  The pair induces the lifted ID
  * A ~ A(:, J_c) P_c of eq. eq:coarseregA.  rows_c = every stride-th grid index
  * in x, y, z from 0, all components, row r = ((c*ny + j)*nz + kz)*nx + i.
+ * If id_factor already started this QR for the current columns, the call
+ * waits for it instead of running it again.
  * Errors: ID_ERR_STATE without want_coarse or without columns. */
 id_status id_coarse_factor(id_sketch* h, int32_t* Jc, double* Pc, int32_t* k_out);
 

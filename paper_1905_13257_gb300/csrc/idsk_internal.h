@@ -245,7 +245,7 @@ struct id_sketch {
   int* d_kout = nullptr;      // 1
   int* d_cand = nullptr;      // n_max: candidate columns (id_factor_restricted)
   double* d_fq = nullptr;     // l k + k + k k: reflectors, tau, R of W(:, J)
-  // coarse workspace (allocated on first id_coarse_factor)
+  // coarse workspace (allocated with the handle when want_coarse)
   double* d_V = nullptr;      // mc x k: reflectors as FP32 pairs (8 bytes each)
   double* d_F = nullptr;      // n_max x k
   double* d_nu2 = nullptr;    // n_max

@@ -270,6 +270,45 @@ def test_coarse_factor_parity(dtype, grid, stride, n, k):
     sk.close()
 
 
+def test_coarse_started_by_factor_and_later_columns():
+    """id_factor starts the coarse QR of the columns seen so far on a side
+    stream; columns streamed afterwards, or a reset, must not be mixed with
+    it: id_coarse_factor then factors all columns seen.  Gap input whose
+    coarse matrix has an oracle pivot margin >= 1e-4 (first such data seed)."""
+    grid, stride, n, k, nc = (16, 12, 16), (2, 2, 2), 90, 8, 3
+    rows = oracle.coarse_rows(grid, nc, stride)
+    for dseed in range(5, 37):
+        A = channel_field(grid, nc, n, seed=dseed, gap_k=k, dtype=torch.float32, device=DEV)
+        An = A.cpu().double().numpy()
+        Jo, Po, ko, margin = oracle.column_id(An[rows], k)
+        J1, _, _, margin1 = oracle.column_id(An[rows][:, :48], k)
+        if margin >= MARGIN and margin1 >= MARGIN:
+            break
+    assert margin >= MARGIN and margin1 >= MARGIN
+    m = A.shape[0]
+    sk = _sk(m=m, n_max=n, k=k, l=16, seed=1, dtype=torch.float32, grid=grid, ncomp=nc,
+             coarse_stride=stride, want_coarse=True)
+    # the started coarse QR is the one id_coarse_factor returns
+    sk.stream_columns(A[:, :48])
+    sk.factor()
+    Jc, Pc, kc = sk.coarse_factor()
+    assert Jc.cpu().tolist()[:kc] == J1.tolist()
+    # columns after id_factor: the coarse QR covers all of them
+    sk.factor()
+    sk.stream_columns(A[:, 48:])
+    Jc, Pc, kc = sk.coarse_factor()
+    assert kc == ko and Jc.cpu().tolist()[:kc] == Jo.tolist()
+    assert np.max(np.abs(Pc.cpu().numpy()[:kc] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
+    # a reset after id_factor, then the same columns again
+    sk.factor()
+    sk.reset()
+    sk.stream_columns(A)
+    sk.factor()
+    Jc2, Pc2, kc2 = sk.coarse_factor()
+    assert kc2 == kc and torch.equal(Jc2, Jc) and torch.equal(Pc2, Pc)
+    sk.close()
+
+
 def test_coarse_rank_deficient():
     grid, nc = (8, 8, 8), 1
     m, n, r = 512, 30, 4
