@@ -305,7 +305,10 @@ def test_coarse_started_by_factor_and_later_columns():
     sk.stream_columns(A)
     sk.factor()
     Jc2, Pc2, kc2 = sk.coarse_factor()
-    assert kc2 == kc and torch.equal(Jc2, Jc) and torch.equal(Pc2, Pc)
+    # started by id_factor on one CTA fewer than id_coarse_factor's own
+    # launch: the per-CTA partial sums differ in rounding order only
+    assert kc2 == kc and torch.equal(Jc2, Jc)
+    assert np.max(np.abs(Pc2.cpu().numpy()[:kc] - Po)) <= 1e-8 * max(1, np.abs(Po).max())
     sk.close()
 
 
