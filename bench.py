@@ -549,7 +549,8 @@ def run_batched(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic channel fields (seeded), resident in HBM",
-        "config": {"workload": "64 channel fields of uneven size in one graph launch: "
+        "config": {"workload": "64 channel fields of uneven size in one graph launch "
+                               "(one persistent work-list sketch launch, batched QRs): "
                                "m ~ U[50k, 2M] (3 x 2ny x ny x 2ny), n ~ U[64, 512], "
                                "k ~ U[10, 80], l = k + 10, seeds 1..64, FP32, "
                                "every other problem BF16 sketch",
@@ -558,11 +559,12 @@ def run_batched(args):
                    "n_range": [min(p["n"] for p in spec), max(p["n"] for p in spec)],
                    "k_range": [min(p["k"] for p in spec), max(p["k"] for p in spec)],
                    "l2": f"inputs larger than L2 ({nbytes / 1e9:.1f} GB); no flush needed"},
-        "roofline": {"kernel": "whole batch (one graph launch; sketch, QR, solve)",
+        "roofline": {"kernel": "whole batch (one graph launch: work-list sketch, slab sums, "
+                               "QRs, solves)",
                      "bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": "of " + kind,
                      "unit": "GB/s", "frac": gbs / peak, "traffic": None},
         "gpu_launches": launches, "clocks": clk,
-        "autotune": {"rows_per_cta": tune_choice,
+        "autotune": {"work_item_mb": tune_choice,
                      "ms_per_launch_by_candidate": {str(k): v for k, v in tune_ms.items()}},
         "k_out_short": sum(1 for (_, _, ko), p in zip(res, spec) if ko < p["k"]),
     }

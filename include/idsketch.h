@@ -267,9 +267,17 @@ typedef struct {
 typedef struct id_batch id_batch;   /* opaque, library-owned */
 
 /* Create a batch on the current device: copies the problem list, creates one
- * sketch state per problem and a pool of up to 8 worker streams (problems
- * are spread over them, largest first, to balance the bytes), and draws each
- * Omega.  cuda_stream: the stream id_batch_run enqueues on (NULL = legacy
+ * sketch state per problem (and draws each Omega), and builds the work
+ * list.  FP32 problems with m >= 128 whose A starts on a 16-byte boundary
+ * with lda a multiple of 4 form the work list: their sketches run as one
+ * persistent tensor-core launch over work items (row ranges of a few MB of
+ * one problem, largest first, taken by one CTA per SM from a device
+ * counter), then one launch sums each problem's W from its items' partial
+ * slabs, one launch runs the pivoted QRs (a cluster of 8 CTAs per problem
+ * with l <= 64, one CTA per problem above), one the solves for P.  Every
+ * other problem (FP64 data, unaligned columns) keeps its own chain of
+ * kernels on a pool of up to 8 worker streams (largest first, to balance
+ * the bytes).  cuda_stream: the stream id_batch_run enqueues on (NULL = legacy
  * default stream).  Errors: ID_ERR_INVALID_ARG (NULL, count outside
  * [1, ID_BATCH_MAX_PROBLEMS], a problem out of its ranges), ID_ERR_OOM,
  * ID_ERR_CUDA. */
@@ -283,8 +291,10 @@ id_status id_batch_create(const id_batch_problem* problems, int32_t count, void*
  *   P    problem b's k_b x n_b FP64 row-major at P + sum_{c<b} k_c n_c
  *   kout problem b's k_out at kout[b]
  * The first run (and a run with other output pointers) captures the work
- * into a CUDA graph, worker streams as parallel branches; later runs replay
- * it.  Errors: ID_ERR_INVALID_ARG (NULL or host output pointers),
+ * into a CUDA graph, the work list and the worker streams as parallel
+ * branches; later runs replay it.  The results of a work-list problem equal
+ * those of one id_sketch handle up to the FP32 summation order of W (the
+ * work items split its rows differently from one handle's CTAs).  Errors: ID_ERR_INVALID_ARG (NULL or host output pointers),
  * ID_ERR_CUDA (the batch is then poisoned: only destroy is valid). */
 id_status id_batch_run(id_batch* b, int32_t* J, double* P, int32_t* kout);
 
@@ -298,17 +308,18 @@ id_status id_batch_wait(id_batch* b, int32_t* kout_host);
 void id_batch_destroy(id_batch* b);
 
 /* Autotuner of the batched form: times the batch's graph with each of the
- * candidate work splits of its sketches (rows_per_cta in {0, 64, 32, 16, 8}:
- * a problem's sketch runs on at most ceil(row blocks / rows_per_cta) CTAs;
- * 0 = one CTA per SM) -- one warm-up and three timed replays each, CUDA events
- * on the batch's private stream -- and keeps the fastest for later
- * id_batch_run calls (with the same output pointers as here, device).
- * Outputs: rows_per_cta (the choice, may be NULL), ms (the 5 average replay
- * times in candidate order, host, may be NULL).  The outputs J, P, kout hold
+ * candidate work splits c in {0, 32, 16, 8, 4} -- one warm-up and three
+ * timed replays each, CUDA events on the batch's private stream -- and keeps
+ * the fastest for later id_batch_run calls (with the same output pointers as
+ * here, device).  With a work list, c is the size of a work item in MB of A
+ * (0: the work list's bytes over 16 items per SM, between 4 and 64 MB);
+ * without one, a problem's sketch runs on at most ceil(row blocks / c) CTAs
+ * (0: one CTA per SM).  Outputs: choice (the chosen c, may be NULL), ms (the
+ * 5 average replay times in candidate order, host, may be NULL).  The outputs J, P, kout hold
  * a complete result of the batch on return.  No counterpart in the paper.
  * Errors: as id_batch_run. */
-id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout,
-                         int32_t* rows_per_cta, float* ms);
+id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout, int32_t* choice,
+                        float* ms);
 
 /* ID of the streamed columns with the skeleton chosen among candidates
  * (the learned proposal's): the pivoted QR of W(:, cand) gives J (pivot

@@ -265,14 +265,16 @@ class IdBatch:
 
     def tune(self):
         """Autotune the work split of the batch's sketches (id_batch_tune):
-        returns (rows_per_cta chosen, {candidate: ms per graph launch})."""
+        returns (the chosen candidate, {candidate: ms per graph launch}); a
+        candidate is the work-item size in MB of A (0: automatic) for a batch
+        with a work list, else the row blocks per CTA of each sketch."""
         choice = C.c_int32()
         ms = (C.c_float * 5)()
         B.check(self.lib.id_batch_tune(self.h, C.c_void_p(self.J.data_ptr()),
                                        C.c_void_p(self.P.data_ptr()),
                                        C.c_void_p(self.kout.data_ptr()), C.byref(choice), ms),
                 "id_batch_tune")
-        return choice.value, dict(zip((0, 64, 32, 16, 8), [float(x) for x in ms]))
+        return choice.value, dict(zip((0, 32, 16, 8, 4), [float(x) for x in ms]))
 
     def wait(self):
         """Wait for the last run: a list of (J_b, P_b, k_out_b), device views."""

@@ -381,7 +381,9 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   const int k = h->k, l = h->l;
   Allocator al;
   al.get(&h->d_status, 1);
-  if (cfg->dtype == ID_F32) al.get(&h->d_wpart, (size_t)h->nsm * kLMax * kTcMaxTiles * 128);
+  if (cfg->dtype == ID_F32)
+    al.get(&h->d_wpart,
+           (size_t)h->nsm * w_width(cfg->l, cfg->want_Y != 0) * kTcMaxTiles * 128);
   al.get(&h->d_omega, (size_t)nm * l);
   al.get(&h->d_W, (size_t)l * nm);
   if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);

@@ -114,6 +114,46 @@ struct SketchArgs {
   int32_t s0;           // first row of Psi drawn by this launch (a multiple of 10)
 };
 
+// Width of the tensor-core sketch's W^T accumulators and partial slabs: 64
+// columns, or 96 when Y is not formed and l > 64 (the whole sketch in one
+// pass over A).
+__host__ __device__ constexpr inline int w_width(int l, bool want_Y) {
+  return (!want_Y && l > kLMax) ? kLMaxW : kLMax;
+}
+
+// ------------------------------------------- batched form (work list)
+// The sketch of one matrix of a batch: all a.l <= 96 rows of Psi in one
+// pass, no Y and no coarse gather.  Its W goes to Wd (row-major, a.l x
+// ncols, leading dimension ncols).
+struct BatchJob {
+  SketchArgs a;
+  int32_t ncols;          // n of the matrix (<= 512)
+  int32_t np;             // bfloat16 pieces of A: 2 (FP32-accurate) or 1 (BF16 form)
+  int32_t prob;           // problem index (its status flag)
+  int32_t item0, nitem;   // its work items, contiguous in the item table
+  int32_t pad;
+  double* Wd;
+};
+// A work item: row blocks rb0 .. rb0 + nrb - 1 of one job, its W^T partials
+// into the FP32 slab at float offset `slab` ([ceil(ncols / 128) * 128][lw],
+// lw = w_width(l, false)).
+struct BatchItem {
+  int64_t rb0;
+  int64_t slab;
+  int32_t nrb, job;
+};
+// Pivoted QR of one batched W (l x n row-major, leading dimension n) and the
+// solve for P, written straight into the batch's packed outputs.
+struct QrJob {
+  double* M;
+  double* R;
+  int32_t* J;
+  int32_t* colpos;
+  int32_t* kout;
+  double* P;
+  int32_t rows, n, k, pad;
+};
+
 // ------------------------------------------------ single-pass ID (Alg. 6)
 // Coarse-to-fine interpolation of one direction at fine index i: the value is
 // (1 - w) f[lo] + w f[hi] with lo, hi coarse indices (a fine index on a coarse
@@ -299,6 +339,17 @@ cudaError_t launch_sketch_simt(const SketchArgs& a, const Window& w, int dtype, 
 cudaError_t launch_sketch_tc(const SketchArgs& a, const Window& w, int npieces, int nsm,
                              int drain_blocks, int* status, cudaStream_t st,
                              KernelTimer* timer = nullptr);
+// Batched form (sketch_tc.cu): the whole work list in one persistent launch
+// (grid CTAs; items taken in `order`; counters[0] the item counter and
+// counters[1 + j] job j's completed items, all zeroed by the caller); the CTA
+// that completes a job's last item sums its slabs into W and runs its QR and
+// solve (qjobs[j]).
+size_t sketch_batch_smem_bytes();
+cudaError_t launch_sketch_batch(const BatchJob* jobs, const CUtensorMap* tmaps,
+                                const BatchItem* items, const int32_t* order, int nitems,
+                                float* slabs, int* counters, const QrJob* qjobs,
+                                double tol_factor, int* stat, int grid, int drain_blocks,
+                                cudaStream_t st);
 cudaError_t launch_cpqr_small(double* M, int rows, int n, int ld, int k, double tol_factor,
                               double* R, int* J, int* colpos, int* kout, cudaStream_t st,
                               bool one_cta = false);

@@ -52,7 +52,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
+#include "cta_qr.cuh"
 #include "df.cuh"
 #include "idsk_internal.h"
 #include "tc_common.cuh"
@@ -78,6 +80,7 @@ constexpr uint32_t PSI_BYTES = LP * TR * 2;          // 16 KB
 constexpr uint32_t OMEGA_TILE_BYTES = LP * TCOLS * 2;  // 16 KB
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t IDESC_W = tc::idesc_bf16(128, LP, 0);   // A^T K-major (K = rows)
+constexpr uint32_t IDESC_W96 = tc::idesc_bf16(128, 96, 0);  // the same, 96 sketch rows
 constexpr uint32_t IDESC_Y = tc::idesc_bf16(128, LP, 1);   // A MN-major (M = rows)
 constexpr int TMEM_Y = kTcMaxTiles * LP;             // Y accumulators after W^T
 
@@ -96,8 +99,8 @@ __device__ long long g_tc_trace[4][8192];
 #endif
 
 // barrier slots
-enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIF1, B_PSIE0, B_PSIE1,
-       B_YF0, B_YF1, B_YE0, B_YE1, B_WF0, B_WE0 = B_WF0 + kTcMaxTiles,
+enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIE0 = B_PSIF0 + 4,
+       B_YF0 = B_PSIE0 + 4, B_YF1, B_YE0, B_YE1, B_WF0, B_WE0 = B_WF0 + kTcMaxTiles,
        B_DONE = B_WE0 + kTcMaxTiles, B_RF0, B_RE0 = B_RF0 + NST, NBAR = B_RE0 + NST };
 
 struct Smem {
@@ -188,12 +191,37 @@ __device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window
   return y;
 }
 
+// Psi(0 .. LWT-1, r) of row r into column rl of a K-major Psi tile (zero
+// past l and past the last row).  The loop over groups of ten stays rolled:
+// unrolled, the longer epilogue code made the sketch slower for every n but
+// the smallest (measured: 2.64 against 2.76 ms per launch with Y; 1.75
+// against 1.77 us per tile at n = 512 without Y; 3.16 against 2.73 us at
+// n = 64, one 128-column tile per row block).
+template <int LWT>
+__device__ __forceinline__ void psi_row(const SketchArgs& a, int64_t r, int rl, uint32_t dst) {
+#pragma unroll 1
+  for (int sb = 0; sb * 10 < LWT; ++sb) {
+    float g[10];
+    if (r < a.m) {
+      gauss10((uint64_t)r, (uint32_t)(sb + a.s0 / 10), kStreamPsi, a.k0, a.k1, a.table, g);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 10; ++f) g[f] = 0.f;
+    }
+#pragma unroll
+    for (int f = 0; f < 10; ++f) {
+      const int s = sb * 10 + f;
+      if (s < LWT)
+        st_shared_u16(dst + swz((uint32_t)s, (uint32_t)rl, 2048u), bf16_bits(s < a.l ? g[f] : 0.f));
+    }
+  }
+}
+
+// Shared-memory carve-up (1024-byte aligned base).  The batched kernel uses
+// the TMA form's layout and keeps its current job's arguments after the
+// abort flag.
 template <int NP, bool TMA>
-__global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
-    sketch_tc_kernel(SketchArgs a, Window w, int drain_blocks, int* __restrict__ status,
-                     const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+__device__ __forceinline__ Smem carve(uint32_t base) {
   Smem S;
   S.pieces = base;
   S.omega = S.pieces + (TMA ? 2u : 2u * NP) * PIECE_BYTES;
@@ -203,65 +231,67 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   S.bars = S.rc + (TMA ? TR * 8u : 0u);
   S.tmem_slot = S.bars + NBAR * 8u;
   S.abort_flag = S.tmem_slot + 4u;
+  return S;
+}
+
+// Barrier set of one row range (thread 0).  again: the barriers of the
+// previous range are invalidated first (every role has left them: the caller
+// synchronised the CTA, and every MMA and TMA copy they tracked completed).
+template <bool TMA>
+__device__ __forceinline__ void init_bars(const Smem& S, bool again) {
   auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
+  if (again)
+    for (int i = 0; i < NBAR; ++i)
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar(i)) : "memory");
+  mbar_init(bar(B_FULL0), NCONV);
+  mbar_init(bar(B_FULL1), NCONV);
+  mbar_init(bar(B_FREE0), 1);
+  mbar_init(bar(B_FREE1), 1);
+  for (int pb = 0; pb < 4; ++pb) {
+    mbar_init(bar(B_PSIF0 + pb), NEPI);
+    mbar_init(bar(B_PSIE0 + pb), 1);
+  }
+  mbar_init(bar(B_YF0), 1);
+  mbar_init(bar(B_YF1), 1);
+  mbar_init(bar(B_YE0), NEPI);
+  mbar_init(bar(B_YE1), NEPI);
+  for (int ct = 0; ct < kTcMaxTiles; ++ct) {
+    mbar_init(bar(B_WF0 + ct), 1);
+    mbar_init(bar(B_WE0 + ct), NEPI);
+  }
+  mbar_init(bar(B_DONE), 1);
+  if (TMA) {
+    for (int st = 0; st < NST; ++st) {
+      mbar_init(bar(B_RF0 + st), 1);
+      mbar_init(bar(B_RE0 + st), NCONV);
+    }
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
 
+// The roles of one CTA over row blocks rb_begin .. rb_begin + nloc - 1 of
+// one window (ncols columns, the first of global index col_base), its W^T
+// partials into the FP32 slab `slab` ([nct * 128][64]).  tm: generic address
+// of the window's tensor map (TMA form); w: the window's segments (register
+// form only).
+template <int NP, bool TMA, bool WY>
+__device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* wp, int ncols,
+                                             int64_t col_base, uint64_t tm, int64_t rb_begin,
+                                             int nloc, float* slab, int drain_blocks,
+                                             const Smem& S, uint32_t tmem, uint8_t* smem_raw) {
+  auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nct = (w.ncols + TCOLS - 1) / TCOLS;
-  const int64_t nrb = (a.m + TR - 1) / TR;
-  const int64_t rb_begin = nrb * blockIdx.x / gridDim.x;
-  const int64_t rb_end = nrb * (blockIdx.x + 1) / gridDim.x;
-  const int nloc = (int)(rb_end - rb_begin);
+  const int nct = (ncols + TCOLS - 1) / TCOLS;
   const int ntile = nloc * nct;
-
-  if (tid == 0) {
-    mbar_init(bar(B_FULL0), NCONV);
-    mbar_init(bar(B_FULL1), NCONV);
-    mbar_init(bar(B_FREE0), 1);
-    mbar_init(bar(B_FREE1), 1);
-    mbar_init(bar(B_PSIF0), NEPI);
-    mbar_init(bar(B_PSIF1), NEPI);
-    mbar_init(bar(B_PSIE0), 1);
-    mbar_init(bar(B_PSIE1), 1);
-    mbar_init(bar(B_YF0), 1);
-    mbar_init(bar(B_YF1), 1);
-    mbar_init(bar(B_YE0), NEPI);
-    mbar_init(bar(B_YE1), NEPI);
-    for (int ct = 0; ct < kTcMaxTiles; ++ct) {
-      mbar_init(bar(B_WF0 + ct), 1);
-      mbar_init(bar(B_WE0 + ct), NEPI);
-    }
-    mbar_init(bar(B_DONE), 1);
-    if (TMA) {
-      for (int st = 0; st < NST; ++st) {
-        mbar_init(bar(B_RF0 + st), 1);
-        mbar_init(bar(B_RE0 + st), NCONV);
-      }
-    }
-    st_volatile_shared(S.abort_flag, 0);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // Omega(window, :) as a K-major bf16 B operand, resident for the kernel
-  constexpr int NT_ALL = TMA ? NTHREADS_TMA : NTHREADS;
-  for (int e = tid; e < kTcMaxTiles * TCOLS * LP; e += NT_ALL) {
-    const int s = e % LP, c = e / LP;
-    float v = 0.f;
-    if (s < a.l && c < w.ncols) v = a.omega[(w.col_base + c) * a.l + s];
-    st_shared_u16(S.omega + (uint32_t)(c >> 7) * OMEGA_TILE_BYTES + swz(s, c & 127, 2048u),
-                  bf16_bits(v));
-  }
-  if (warp == MMA_WARP) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     S.tmem_slot),
-                 "n"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  uint32_t tmem;
-  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
+  // Widths and the Psi ring: with Y, W^T tiles of 64 columns and two Psi
+  // buffers; without Y, W^T tiles of 64 or 96 columns (l <= 96 in one pass:
+  // the Y accumulators' TMEM is free) and four Psi buffers in the shared
+  // memory that Omega would use (and the usual Psi buffers after it).
+  constexpr bool wy = WY;   // a.want_Y, fixed per instantiation
+  const int lw = WY ? LP : w_width(a.l, false);
+  constexpr int npsi = WY ? 2 : 4;
+  const uint32_t psi0 = WY ? S.psi : S.omega;
+  const uint32_t psi_bytes = (uint32_t)lw * TR * 2u;
 
   // W^T tile ct is flushed after row block i when drain_due(i, ct): every
   // drain_blocks row blocks, the tiles offset from one another so that the
@@ -337,9 +367,9 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
               lo_keep[(j * 4 + g) * 2 + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
             }
           }
-          if (gather && wc < w.ncols)
+          if (gather && wc < ncols)
             gather_column(raw + cl * TR, rcs, rq,
-                          reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + wc));
+                          reinterpret_cast<float*>(a.Ac) + a.cg.mc * (col_base + wc));
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_RE0 + st));
         }
@@ -376,6 +406,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     // rows of a half tile.  The loads of the next half tile are issued before
     // the current one is split and stored (ping-pong register buffers), with
     // plain address arithmetic on the window's single segment when it has one.
+    const Window& w = *wp;
     const int row_off = lane * 4;
     const bool one_seg = (w.nseg == 1);
     const float* seg_base = reinterpret_cast<const float*>(w.seg[0].ptr);
@@ -456,35 +487,24 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     auto gen_psi = [&](int i, int pb) {
       const int64_t r = (rb_begin + i) * TR + rl;
-      const uint32_t dst = S.psi + (uint32_t)pb * PSI_BYTES;
-      for (int sb = 0; sb * 10 < LP; ++sb) {
-        float g[10];
-        if (r < a.m) {
-          gauss10((uint64_t)r, (uint32_t)(sb + a.s0 / 10), kStreamPsi, a.k0, a.k1, a.table, g);
-        } else {
-#pragma unroll
-          for (int f = 0; f < 10; ++f) g[f] = 0.f;
-        }
-#pragma unroll
-        for (int f = 0; f < 10; ++f) {
-          const int s = sb * 10 + f;
-          if (s < LP) st_shared_u16(dst + swz((uint32_t)s, (uint32_t)rl, 2048u),
-                                    bf16_bits(s < a.l ? g[f] : 0.f));
-        }
-      }
+      const uint32_t dst = psi0 + (uint32_t)pb * psi_bytes;
+      if (WY || lw == 64)
+        psi_row<64>(a, r, rl, dst);
+      else
+        psi_row<96>(a, r, rl, dst);
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_PSIF0 + pb));
     };
-    for (int i = 0; i < 2 && i < nloc; ++i) gen_psi(i, i);
+    for (int i = 0; i < npsi && i < nloc; ++i) gen_psi(i, i);
     uint32_t wpar = 0, wseen = 0;   // per W^T tile: flush-count parity, flushed before
     for (int i = 0; i < nloc; ++i) {
-      const int pb = i & 1;
+      const int pb = i & (npsi - 1), yb = i & 1;
       // a later window adds into Y: its old values of row block i + 2 are
       // prefetched into L2 now (the warp's 32 rows of every sketch column),
       // so that the read-modify-write at the drain waits for L2, not HBM
       // (a bulk prefetch needs 16-byte aligned addresses: m a multiple of 4)
-      if (a.want_Y && a.y_accumulate && (a.m & 3) == 0 && i + 2 < nloc) {
+      if (wy && a.y_accumulate && (a.m & 3) == 0 && i + 2 < nloc) {
         const int64_t r2 = (rb_begin + i + 2) * TR + q * 32;
         if (r2 + 32 <= a.m)
           for (int j = lane; j < a.l; j += 32)
@@ -503,50 +523,58 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        // the tile's 128 x 64 partials into registers; the accumulator then
-        // goes back to the MMAs while the partials are added to this CTA's
-        // private FP32 slab wpart[cta][c][s] (the first flush of a tile
-        // stores, later ones add in L2, four entries per reduction; each slab
-        // entry is written by one thread only, in program order, so the sum
-        // has a fixed order)
-        float v[2][32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP), v[0]);
-        tmem_ld32(tmem + lane_base + (uint32_t)(ct * LP + 32), v[1]);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_WE0 + ct));
+        // the tile's 128 x lw partials into registers (32 columns at a
+        // time); the accumulator goes back to the MMAs once the last chunk
+        // is in registers, and the partials are added to this range's FP32
+        // slab [c][s] (the first flush of a tile stores, later ones add in
+        // L2, four entries per reduction; each slab entry is written by one
+        // thread only, in program order, so the sum has a fixed order)
         const uint64_t keep = policy_evict_last();
-        float* dst =
-            a.wpart + ((int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) + ct * TCOLS + rl) * LP;
+        float* dst = slab + (int64_t)(ct * TCOLS + rl) * lw;
         const bool first = !((wseen >> ct) & 1u);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        auto put = [&](const float(&v)[32], int c0) {
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             if (first)
-              st_v4_f32_hint(dst + h * 32 + j, v[h][j], v[h][j + 1], v[h][j + 2], v[h][j + 3],
-                             keep);
+              st_v4_f32_hint(dst + c0 + j, v[j], v[j + 1], v[j + 2], v[j + 3], keep);
             else
-              red_add_v4_f32(dst + h * 32 + j, v[h][j], v[h][j + 1], v[h][j + 2], v[h][j + 3],
-                             keep);
+              red_add_v4_f32(dst + c0 + j, v[j], v[j + 1], v[j + 2], v[j + 3], keep);
           }
+        };
+        float v[2][32];
+        const uint32_t tcol = tmem + lane_base + (uint32_t)(ct * lw);
+        tmem_ld32(tcol, v[0]);
+        tmem_ld32(tcol + 32, v[1]);
+        if (lw == 64) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_WE0 + ct));
+        }
+        put(v[0], 0);
+        put(v[1], 32);
+        if (lw == 96) {
+          tmem_ld32(tcol + 64, v[0]);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_WE0 + ct));
+          put(v[0], 64);
         }
         wpar ^= 1u << ct;
         wseen |= 1u << ct;
       }
       if (!wok) break;
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i);
-      if (!mbar_wait(bar(B_YF0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
-      tc_fence_after();
-      if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 1);
-      {
+      if (wy) {   // Y of row block i: accumulator yb
+        if (!mbar_wait(bar(B_YF0 + yb), (i >> 1) & 1, S.abort_flag, 256)) break;
+        tc_fence_after();
+        if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 1);
         const int64_t r = (rb_begin + i) * TR + rl;
         float* Y = reinterpret_cast<float*>(a.Y);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(TMEM_Y + pb * LP + h * 32), v);
-          if (a.want_Y && r < a.m) {
+          tmem_ld32(tmem + lane_base + (uint32_t)(TMEM_Y + yb * LP + h * 32), v);
+          if (r < a.m) {
             float* yr = Y + r + (int64_t)(h * 32) * a.m;
             if (a.y_accumulate) {   // all loads in flight before the stores
               float old[32];
@@ -561,14 +589,14 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
               if (h * 32 + j < a.l) __stcs(yr + (int64_t)j * a.m, v[j]);
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_YE0 + yb));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(B_YE0 + pb));
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 2);
-      if (i + 2 < nloc) {
-        if (!mbar_wait(bar(B_PSIE0 + pb), (i >> 1) & 1, S.abort_flag, 256)) break;
-        gen_psi(i + 2, pb);
+      if (i + npsi < nloc) {   // Psi buffer pb is free once row block i's MMAs completed
+        if (!mbar_wait(bar(B_PSIE0 + pb), (i / npsi) & 1, S.abort_flag, 256)) break;
+        gen_psi(i + npsi, pb);
       }
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 3);
     }
@@ -577,15 +605,16 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     uint32_t accw = 0;    // bit ct: W^T accumulator of tile ct holds data
     uint32_t wpend = 0;   // bit ct: tile ct handed to the epilogue, not yet read out
     uint32_t wpar = 0;    // bit ct: parity of the flushes of tile ct handed out
+    const uint32_t idesc_w = lw == 96 ? IDESC_W96 : IDESC_W;
     int t = 0;
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
-      const int pb = i & 1;
-      if (!mbar_wait(bar(B_PSIF0 + pb), (i >> 1) & 1, S.abort_flag)) break;
-      if (i >= 2 && !mbar_wait(bar(B_YE0 + pb), ((i >> 1) - 1) & 1, S.abort_flag)) break;
+      const int pb = i & (npsi - 1), yb = i & 1;
+      if (!mbar_wait(bar(B_PSIF0 + pb), (i / npsi) & 1, S.abort_flag)) break;
+      if (wy && i >= 2 && !mbar_wait(bar(B_YE0 + yb), ((i >> 1) - 1) & 1, S.abort_flag)) break;
       tc_fence_after();
-      const uint32_t psi_s = S.psi + (uint32_t)pb * PSI_BYTES;
-      const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + pb * LP);
+      const uint32_t psi_s = psi0 + (uint32_t)pb * psi_bytes;
+      const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + yb * LP);
       for (int ct = 0; ct < nct; ++ct, ++t) {
         const int b = t & 1;
         if (!TMA && !mbar_wait(bar(B_FULL0 + b), (t >> 1) & 1, S.abort_flag)) {
@@ -601,7 +630,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         }
         tc_fence_after();
         const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
-        const uint32_t wtm = tmem + (uint32_t)(ct * LP);
+        const uint32_t wtm = tmem + (uint32_t)(ct * lw);
         const uint32_t om = S.omega + (uint32_t)ct * OMEGA_TILE_BYTES;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
@@ -627,13 +656,15 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {   // W^T: K = 16 rows per instruction
             const uint64_t ko = (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);   // bytes >> 4
-            mma_bf16(wtm, dA + ko, dPsi + ko, IDESC_W, acc0 | (uint32_t)(p | kk));
+            mma_bf16(wtm, dA + ko, dPsi + ko, idesc_w, acc0 | (uint32_t)(p | kk));
           }
+          if (wy) {   // without Y the pieces feed the W^T product only
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {   // Y: K = 16 columns per instruction
-            const uint64_t ko = (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-            mma_bf16(ytm, dAy + (uint64_t)(kk * 256), dOm + ko, IDESC_Y,
-                     (uint32_t)(ct | p | kk));
+            for (int kk = 0; kk < 8; ++kk) {   // Y: K = 16 columns per instruction
+              const uint64_t ko = (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+              mma_bf16(ytm, dAy + (uint64_t)(kk * 256), dOm + ko, IDESC_Y,
+                       (uint32_t)(ct | p | kk));
+            }
           }
           if (TMA) mma_commit(bar(B_FREE0 + (u & 1)));
           TC_TRACE(1, 2 * u + 1);
@@ -649,7 +680,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
         }
       }
       if (!ok) break;
-      mma_commit(bar(B_YF0 + pb));
+      if (wy) mma_commit(bar(B_YF0 + yb));
       mma_commit(bar(B_PSIE0 + pb));
     }
     // every issued MMA has completed before the TMEM is released
@@ -663,7 +694,6 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     }
   } else if (TMA && warp == PROD_WARP && lane == 0) {
     // -------------------------------------------------------- TMA producer
-    const uint64_t tm = reinterpret_cast<uint64_t>(&tmap);
     const uint64_t stream_once = policy_evict_first();
     int u = 0;
     bool ok = true;
@@ -683,15 +713,197 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
       }
     }
   }
+}
+
+// Omega(window, :) as a K-major bf16 B operand of the Y product, resident
+// for the row range.
+template <bool TMA>
+__device__ __forceinline__ void fill_omega(const Smem& S, const SketchArgs& a, int ncols,
+                                           int64_t col_base) {
+  constexpr int NT_ALL = TMA ? NTHREADS_TMA : NTHREADS;
+  for (int e = threadIdx.x; e < kTcMaxTiles * TCOLS * LP; e += NT_ALL) {
+    const int s = e % LP, c = e / LP;
+    float v = 0.f;
+    if (s < a.l && c < ncols) v = a.omega[(col_base + c) * a.l + s];
+    st_shared_u16(S.omega + (uint32_t)(c >> 7) * OMEGA_TILE_BYTES + swz(s, c & 127, 2048u),
+                  bf16_bits(v));
+  }
+}
+
+__device__ __forceinline__ void tmem_alloc_all(const Smem& S) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   S.tmem_slot),
+               "n"(TMEM_COLS)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+               "n"(TMEM_COLS)
+               : "memory");
+}
+
+// One window of one matrix: CTA b takes the contiguous row blocks
+// [nrb b / G, nrb (b + 1) / G) of the G CTAs, its W^T partials into slab b.
+template <int NP, bool TMA, bool WY>
+__global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
+    sketch_tc_kernel(const __grid_constant__ SketchArgs a, const __grid_constant__ Window w,
+                     int drain_blocks, int* __restrict__ status,
+                     const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ uint8_t smem_raw[];
+  const Smem S = carve<NP, TMA>((smem_u32(smem_raw) + 1023u) & ~1023u);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t nrb = (a.m + TR - 1) / TR;
+  const int64_t rb_begin = nrb * blockIdx.x / gridDim.x;
+  const int64_t rb_end = nrb * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    st_volatile_shared(S.abort_flag, 0);
+    init_bars<TMA>(S, false);
+  }
+  if (WY) fill_omega<TMA>(S, a, w.ncols, w.col_base);
+  if (warp == MMA_WARP) tmem_alloc_all(S);
+  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == MMA_WARP) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "n"(TMEM_COLS)
-                 : "memory");
-  }
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
+  sketch_roles<NP, TMA, WY>(a, &w, w.ncols, w.col_base, reinterpret_cast<uint64_t>(&tmap), rb_begin,
+                        (int)(rb_end - rb_begin),
+                        a.wpart + (int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) *
+                                      w_width(a.l, a.want_Y != 0),
+                        drain_blocks,
+                        S, tmem, smem_raw);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == MMA_WARP) tmem_free_all(tmem);
   if (tid == 0 && ld_volatile_shared(S.abort_flag)) atomicOr(status, 1);
+}
+
+// Batched form, the last step of one matrix: W = the sum of its items'
+// slabs in item order (deterministic, FP32 pairs, read past L1: other SMs
+// wrote them), then the pivoted QR of W and the solve for P into the
+// batch's outputs, all by this CTA (shared scratch in the free buffers).
+__device__ __forceinline__ void finish_job(const BatchJob& jb, const BatchItem* __restrict__ items,
+                                           const float* __restrict__ slabs, const QrJob& q,
+                                           double tol_factor, uint8_t* scratch) {
+  const int l = jb.a.l, n = jb.ncols, lw = w_width(l, false);
+  for (int e = threadIdx.x; e < l * n; e += NTHREADS_TMA) {
+    const int c = e / l, s = e - c * l;
+    float hi = 0.f, lo = 0.f;
+    for (int q0 = 0; q0 < jb.nitem; q0 += 8) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = q0 + u < jb.nitem
+                   ? __ldcg(slabs + items[jb.item0 + q0 + u].slab + (int64_t)c * lw + s)
+                   : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) df_add(hi, lo, x[u], 0.f);
+    }
+    jb.Wd[(int64_t)s * n + c] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  qr::QrShared& sh = *reinterpret_cast<qr::QrShared*>(scratch);
+  qr::cta_pivoted_qr<NTHREADS_TMA>(q.M, q.rows, q.n, q.n, q.k, tol_factor, q.R, q.J, q.colpos,
+                                   q.kout, sh);
+  __syncthreads();
+  double* r11 = reinterpret_cast<double*>(scratch + 4096);
+  double* rdiag = r11 + kLMaxW * kLMaxW;
+  int* Js = reinterpret_cast<int*>(rdiag + kLMaxW);
+  const int kk = qr::solve_setup(q.R, q.J, q.kout, q.n, r11, Js, rdiag);
+  for (int j = threadIdx.x >> 5; j < q.n; j += NTHREADS_TMA / 32)
+    qr::solve_column(j, q.R, q.colpos, q.k, kk, q.n, q.P, r11, rdiag);
+  __syncthreads();
+}
+
+// Batched form in one persistent launch: a work list of row ranges (items)
+// over the sketches (jobs) of many matrices, one CTA per SM.  A CTA takes the
+// next item from a global counter (jobs in order of decreasing QR work, each
+// job's items in row order), sets up the job's arguments and a fresh barrier
+// set, runs the roles over the item's row blocks into the item's W^T slab,
+// and synchronises.  The CTA that completes a job's last item (counted per
+// job after its slab writes are fenced) sums the job's slabs into W and runs
+// its pivoted QR and solve, while the other CTAs go on with later items.  The
+// TMEM stays allocated throughout.  Every wait stays bounded: a CTA that
+// gives up raises its job's problem flag and stops taking items.
+__global__ void __launch_bounds__(NTHREADS_TMA, 1)
+    sketch_batch_kernel(const BatchJob* __restrict__ jobs, const CUtensorMap* __restrict__ tmaps,
+                        const BatchItem* __restrict__ items, const int32_t* __restrict__ order,
+                        int nitems, float* __restrict__ slabs, int* __restrict__ counters,
+                        const QrJob* __restrict__ qjobs, double tol_factor,
+                        int* __restrict__ stat, int drain_blocks) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t sbase = smem_u32(smem_raw);
+  const Smem S = carve<1, true>((sbase + 1023u) & ~1023u);
+  const uint32_t s_args = (S.abort_flag + 4u + 15u) & ~15u;       // SketchArgs of the job
+  const uint32_t s_item = s_args + (uint32_t)sizeof(SketchArgs);   // item index
+  const uint32_t s_last = s_item + 4u;                             // the item completed its job
+  SketchArgs* args = reinterpret_cast<SketchArgs*>(smem_raw + (s_args - sbase));
+  uint8_t* scratch = smem_raw + (S.pieces - sbase);   // free between items
+  int* job_done = counters + 1;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) st_volatile_shared(S.abort_flag, 0);
+  if (warp == MMA_WARP) tmem_alloc_all(S);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
+  for (int round = 0;; ++round) {
+    if (tid == 0) {
+      const int q = atomicAdd(counters, 1);
+      st_volatile_shared(s_item, q < nitems ? order[q] : -1);
+    }
+    __syncthreads();
+    {
+      const int it = ld_volatile_shared(s_item);
+      if (it < 0) break;
+      const BatchItem item = items[it];
+      const BatchJob& jb = jobs[item.job];
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&jb.a);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(args);
+      for (int e = tid; e < (int)(sizeof(SketchArgs) / 4); e += NTHREADS_TMA) dst[e] = src[e];
+      if (tid == 0) init_bars<true>(S, round > 0);
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      const uint64_t tm = reinterpret_cast<uint64_t>(tmaps + item.job);
+      if (jb.np == 2)
+        sketch_roles<2, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
+                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw);
+      else
+        sketch_roles<1, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
+                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw);
+    }
+    if (warp >= NCONV && warp < MMA_WARP) __threadfence();   // the slab writes, GPU-wide
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const int it = ld_volatile_shared(s_item);
+    const int job = items[it].job;
+    if (ld_volatile_shared(S.abort_flag)) {
+      if (tid == 0) atomicOr(stat + jobs[job].prob, 1);
+      break;
+    }
+    if (tid == 0) {
+      __threadfence();
+      const int done = atomicAdd(job_done + job, 1) + 1;
+      st_volatile_shared(s_last, done == jobs[job].nitem ? 1 : 0);
+    }
+    __syncthreads();
+    if (ld_volatile_shared(s_last)) {
+      __threadfence();
+      finish_job(jobs[job], items, slabs, qjobs[job], tol_factor, scratch);
+      fence_proxy_async();   // the scratch's generic writes before the next TMA writes
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == MMA_WARP) tmem_free_all(tmem);
 }
 
 // W(:, window) = sum over CTAs of their slabs, in CTA order (deterministic),
@@ -699,14 +911,14 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
 // dependent FP64 additions per entry), eight slabs' loads in flight at a
 // time.  A CTA whose row range is empty never wrote its slab and is skipped
 // (only possible when there are fewer row blocks than CTAs).
-__global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, int l, int ncols,
-                                    int64_t nrb, double* __restrict__ W, int64_t ldw,
+__global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, int l, int lw,
+                                    int ncols, int64_t nrb, double* __restrict__ W, int64_t ldw,
                                     int64_t col_base) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * ncols) return;
   const int c = e / l, s = e - c * l;
-  const float* src = wpart + (int64_t)c * LP + s;
-  const int64_t slab = (int64_t)kTcMaxTiles * TCOLS * LP;
+  const float* src = wpart + (int64_t)c * lw + s;
+  const int64_t slab = (int64_t)kTcMaxTiles * TCOLS * lw;
   const bool all_rows = nrb >= nslab;   // then every CTA owns at least one row block
   float hi = 0.f, lo = 0.f;
   for (int b0 = 0; b0 < nslab; b0 += 8) {
@@ -738,17 +950,17 @@ bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
   return make_tmap_f32_2d(w.seg[0].ptr, a.m, w.seg[0].ncols, w.seg[0].ld, TR, 32, tm);
 }
 
-template <int NP, bool TMA>
+template <int NP, bool TMA, bool WY>
 cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int drain_blocks,
                            int* status, const CUtensorMap& tm, cudaStream_t st,
                            KernelTimer* timer) {
   const size_t sm = tc_smem_bytes<NP, TMA>();
-  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA>,
+  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA, WY>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
-  sketch_tc_kernel<NP, TMA><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(a, w, drain_blocks,
-                                                                              status, tm);
+  sketch_tc_kernel<NP, TMA, WY><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(
+      a, w, drain_blocks, status, tm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (timer) e = timer->mark(st);
   return e;
@@ -773,11 +985,15 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   if (w.ncols <= 0) return cudaSuccess;
   if (w.ncols > kTcMaxTiles * TCOLS || a0.l > kLMaxW || a0.s0 % 10 != 0)
     return cudaErrorInvalidValue;
-  if (a0.l > LP) {
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  const bool tma = make_tmap(a0, w, &tm);
+  if (a0.l > LP && a0.want_Y) return cudaErrorInvalidValue;
+  if (a0.l > LP && !tma) {
     if (a0.s0 != 0) return cudaErrorInvalidValue;
-    // a wide sketch (W only): one launch per kPassRows rows of Psi, the
-    // coarse rows gathered by the first
-    if (a0.want_Y) return cudaErrorInvalidValue;
+    // a wide sketch (W only) in the register form: one launch per kPassRows
+    // rows of Psi, the coarse rows gathered by the first (the TMA form takes
+    // all l <= 96 rows in one pass)
     for (int s0 = 0; s0 < a0.l; s0 += kPassRows) {
       SketchArgs a = a0;
       a.s0 = s0;
@@ -792,21 +1008,52 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   const SketchArgs& a = a0;
   const int64_t nrb = (a.m + TR - 1) / TR;
   const int grid = (int)std::min<int64_t>(nrb, nsm);
-  CUtensorMap tm;
-  memset(&tm, 0, sizeof(tm));
-  const bool tma = make_tmap(a, w, &tm);
   cudaError_t e;
-  if (npieces == 1)
-    e = tma ? launch_variant<1, true>(a, w, grid, drain_blocks, status, tm, st, timer)
-            : launch_variant<1, false>(a, w, grid, drain_blocks, status, tm, st, timer);
-  else
-    e = tma ? launch_variant<2, true>(a, w, grid, drain_blocks, status, tm, st, timer)
-            : launch_variant<2, false>(a, w, grid, drain_blocks, status, tm, st, timer);
+  auto go = [&](auto np, auto tmaf, auto wy) {
+    return launch_variant<decltype(np)::value, decltype(tmaf)::value, decltype(wy)::value>(
+        a, w, grid, drain_blocks, status, tm, st, timer);
+  };
+  using T = std::true_type;
+  using F = std::false_type;
+  using N1 = std::integral_constant<int, 1>;
+  using N2 = std::integral_constant<int, 2>;
+  if (a.want_Y) {
+    if (npieces == 1)
+      e = tma ? go(N1(), T(), T()) : go(N1(), F(), T());
+    else
+      e = tma ? go(N2(), T(), T()) : go(N2(), F(), T());
+  } else {
+    if (npieces == 1)
+      e = tma ? go(N1(), T(), F()) : go(N1(), F(), F());
+    else
+      e = tma ? go(N2(), T(), F()) : go(N2(), F(), F());
+  }
   if (e != cudaSuccess) return e;
   const int tot = a.l * w.ncols;
-  wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(a.wpart, grid, a.l, w.ncols, nrb, a.W,
-                                                         a.ldw, w.col_base);
+  wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(
+      a.wpart, grid, a.l, w_width(a.l, a.want_Y != 0), w.ncols, nrb, a.W, a.ldw, w.col_base);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+size_t sketch_batch_smem_bytes() {
+  return tc_smem_bytes<1, true>() + 16 + sizeof(SketchArgs) + 16;
+}
+
+cudaError_t launch_sketch_batch(const BatchJob* jobs, const CUtensorMap* tmaps,
+                                const BatchItem* items, const int32_t* order, int nitems,
+                                float* slabs, int* counters, const QrJob* qjobs,
+                                double tol_factor, int* stat, int grid, int drain_blocks,
+                                cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t sm = sketch_batch_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(sketch_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  sketch_batch_kernel<<<grid, NTHREADS_TMA, sm, st>>>(jobs, tmaps, items, order, nitems, slabs,
+                                                      counters, qjobs, tol_factor, stat,
+                                                      drain_blocks);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -2,11 +2,19 @@
 graph-launched batch against the oracle's randomized ID (Algorithm 4,
 Sec. 2.4) on the same Psi and Omega, and against one handle per problem.
 
+FP32 problems with aligned columns run in the work-list form (one persistent
+launch over row ranges of all of them; the CTA that completes a matrix's
+last range sums its W and runs its QR and solve); FP64 and unaligned
+problems on their own graph branches.
+
 Bars as for the single-handle randomized ID: k_out equal, P(:, J) = I exactly,
 J equal where the oracle's pivot margin is >= 1e-4 (below it, the error of
 the returned skeleton within 1.05x the oracle's), P within 1e-3 (FP32 data,
 FP32-accurate sketch) or 1e-10 (FP64) of the oracle's, relative to max(1,
-max|P|); against one handle on the same data J equal and P within 1e-9.
+max|P|).  Against one handle on the same data: J equal where the margin
+allows; P within 1e-9 for FP64 data (the same kernels and split), within the
+FP32 bar for FP32 data (the work items split the rows of W's sums
+differently from one handle's CTAs).
 """
 import ctypes as C
 
@@ -55,7 +63,7 @@ def oracle_id(p):
 def check_against_oracle(p, J, P, kout):
     """J equal to the oracle's when its pivot margin is >= 1e-4; below that
     (pivots within rounding of a tie) a valid skeleton whose error on A is
-    the oracle's within 1.05x (the equal-error bar)."""
+    the oracle's within 1.05x (the equal-error bar).  Returns the margin."""
     Jo, Po, ko, margin = oracle_id(p)
     k = p["k"]
     assert kout == ko == k
@@ -66,10 +74,11 @@ def check_against_oracle(p, J, P, kout):
         fo, _ = oracle.recon_error(An, Jo, Po)
         fg, _ = oracle.recon_error(An, Jg, Pg)
         assert fg <= 1.05 * fo, (margin, fg, fo)
-        return
+        return margin
     assert Jg.tolist() == Jo.tolist()
     tol = 1e-10 if p["A"].dtype == torch.float64 else 1e-3
     assert np.max(np.abs(Pg - Po)) <= tol * max(1.0, np.max(np.abs(Po)))
+    return margin
 
 
 def test_batch_matches_oracle_and_single_handles():
@@ -80,16 +89,19 @@ def test_batch_matches_oracle_and_single_handles():
     res = bt.wait()
     assert len(res) == len(probs)
     for p, (J, P, kout) in zip(probs, res):
-        check_against_oracle(p, J, P, kout)
+        margin = check_against_oracle(p, J, P, kout)
         A = p["A"]
         sk = IdSketch(m=A.shape[0], n_max=A.shape[1], k=p["k"], l=p["l"], seed=p["seed"],
                       dtype=A.dtype, prec=p["prec"], want_Y=False)
         sk.stream_columns(A)
         J1, P1, k1 = sk.factor()
         assert k1 == kout
-        assert J1.tolist() == J.tolist()
+        if margin >= MARGIN:
+            assert J1.tolist() == J.tolist()
         P1n = P1.cpu().numpy()
-        assert np.max(np.abs(P.cpu().numpy() - P1n)) <= 1e-9 * max(1.0, np.abs(P1n).max())
+        tol = 1e-9 if A.dtype == torch.float64 else 1e-3
+        if J1.tolist() == J.tolist():
+            assert np.max(np.abs(P.cpu().numpy() - P1n)) <= tol * max(1.0, np.abs(P1n).max())
         sk.close()
     bt.close()
 
@@ -106,7 +118,10 @@ def test_batch_replay_reads_new_data_and_counts_launches():
     bt.run()
     bt.wait()
     per_run = lib.id_kernel_launches() - l0
-    assert per_run >= 3 * len(probs)
+    # the FP32 problems share one persistent launch (sketches, slab sums, QRs
+    # and solves); each FP64 problem has its own chain of kernels
+    n64 = sum(1 for p in probs if p["A"].dtype == torch.float64)
+    assert 1 + 2 * n64 <= per_run <= 1 + 4 * n64
     # overwrite the data in place: the replay must see the new matrices
     for i, p in enumerate(probs):
         grid, n, k = CASES[i][0], CASES[i][1], CASES[i][2]
@@ -174,6 +189,33 @@ def test_batch_autotuner_keeps_the_results():
     choice, ms = bt.tune()
     assert choice in ms and all(v > 0 for v in ms.values())
     assert ms[choice] == min(ms.values())
+    bt.run()
+    for p, (J, P, kout) in zip(probs, bt.wait()):
+        check_against_oracle(p, J, P, kout)
+    bt.close()
+
+
+def test_batch_mixed_forms_and_item_sizes():
+    """An FP32 problem whose leading dimension is not a multiple of 4 leaves
+    the work list for its own branch, beside work-list problems and an FP64
+    one; every candidate work-item size of the tuner gives the oracle's
+    result (the tuner leaves the last result in the outputs), and so does a
+    replay with the chosen size."""
+    from paper_1905_13257_gb300 import IdBatch
+    probs = []
+    for i, (grid, n, k, l, dtype, prec) in enumerate(CASES[:5]):
+        A = channel_field(grid, 3, n, seed=90 + i, gap_k=k, dtype=dtype, device=DEV)
+        probs.append(dict(A=A, k=k, l=l, seed=300 + i, prec=prec))
+    m = probs[1]["A"].shape[0]
+    buf = torch.zeros(probs[1]["A"].shape[1], m + 1, dtype=torch.float32, device=DEV)
+    buf[:, :m] = probs[1]["A"].T
+    probs[1]["A"] = buf[:, :m].T            # column-major, lda = m + 1
+    assert probs[1]["A"].stride() == (1, m + 1)
+    bt = IdBatch(probs)
+    choice, ms = bt.tune()
+    assert set(ms) == {0, 32, 16, 8, 4} and ms[choice] == min(ms.values())
+    for p, (J, P, kout) in zip(probs, bt.wait()):
+        check_against_oracle(p, J, P, kout)
     bt.run()
     for p, (J, P, kout) in zip(probs, bt.wait()):
         check_against_oracle(p, J, P, kout)

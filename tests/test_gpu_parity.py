@@ -153,11 +153,14 @@ def test_factor_parity_gap_input(dtype, grid, n, k, l):
     sk.close()
 
 
-@pytest.mark.parametrize("prec", ["exact", "bf16"])
-def test_wide_sketch_factor(prec):
-    """l = 90, k = 80 (FP32 data, W only): the sketch in two passes of Psi
-    rows (0-59, 60-89), the one-CTA pivoted QR of the 90-row W and the solve
-    for 80 pivots, against the oracle on the same Psi."""
+@pytest.mark.parametrize("prec,form", [("exact", "tma"), ("bf16", "tma"), ("exact", "register")])
+def test_wide_sketch_factor(prec, form, monkeypatch):
+    """l = 90, k = 80 (FP32 data, W only): the sketch in one pass with 96-wide
+    W^T accumulators (TMA feed) or in two passes of Psi rows 0-59, 60-89
+    (register feed), the one-CTA pivoted QR of the 90-row W and the solve for
+    80 pivots, against the oracle on the same Psi."""
+    if form == "register":
+        monkeypatch.setenv("IDSKETCH_SKETCH_TMA", "0")
     grid, n, k, l = (16, 12, 16), 240, 80, 90
     A = channel_field(grid, 3, n, seed=7, gap_k=k, dtype=torch.float32, device=DEV)
     m = A.shape[0]
