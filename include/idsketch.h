@@ -91,10 +91,12 @@ typedef struct id_sketch id_sketch;   /* opaque, library-owned */
  * Passage: Algorithm 4 steps 2-3 (Gaussian Omega, l = k + p; Sec. 2.2).
  * cuda_stream may be NULL (legacy default stream).
  * Sketch width: l <= 64 for every form.  FP32 data without Y may take
- * 64 < l <= 96 (k up to 86 at p = 10): the tensor-core sketch then forms W in
- * passes of 60 rows of Psi over each window (one more read of the window per
- * pass), the pivoted QR and the solve take the wider W, and the coarse-grid
- * QR, the error pass and the single-pass ID keep k <= 64.
+ * 64 < l <= 96 (k up to 86 at p = 10): the tensor-core sketch then forms W
+ * in one pass with 96-wide accumulators when the window is one buffer with
+ * 16-byte aligned columns, else in passes of 60 rows of Psi (one more read
+ * of the window per pass); the pivoted QR and the solve take the wider W,
+ * and the coarse-grid QR, the error pass and the single-pass ID keep
+ * k <= 64.
  * Errors: ID_ERR_INVALID_ARG for an inconsistent config (m <= 0, n_max <= 0,
  * k < 1, k > l, l > 96, grid/ncomp not matching m when want_coarse, a coarse
  * stride < 1, reserved fields != 0), ID_ERR_UNSUPPORTED (l > 64 with FP64
@@ -269,15 +271,14 @@ typedef struct id_batch id_batch;   /* opaque, library-owned */
 /* Create a batch on the current device: copies the problem list, creates one
  * sketch state per problem (and draws each Omega), and builds the work
  * list.  FP32 problems with m >= 128 whose A starts on a 16-byte boundary
- * with lda a multiple of 4 form the work list: their sketches run as one
- * persistent tensor-core launch over work items (row ranges of a few MB of
- * one problem, largest first, taken by one CTA per SM from a device
- * counter), then one launch sums each problem's W from its items' partial
- * slabs, one launch runs the pivoted QRs (a cluster of 8 CTAs per problem
- * with l <= 64, one CTA per problem above), one the solves for P.  Every
- * other problem (FP64 data, unaligned columns) keeps its own chain of
- * kernels on a pool of up to 8 worker streams (largest first, to balance
- * the bytes).  cuda_stream: the stream id_batch_run enqueues on (NULL = legacy
+ * with lda a multiple of 4 form the work list, run as one persistent
+ * tensor-core launch (one CTA per SM): work items (row ranges of a few MB of
+ * one problem; problems in order of decreasing QR work) are taken from a
+ * device counter, and the CTA that completes a problem's last item sums W
+ * from the items' partial slabs and runs the problem's pivoted QR and solve
+ * for P while the other CTAs go on with later items.  Every other problem
+ * (FP64 data, unaligned columns) keeps its own chain of kernels on a pool of
+ * up to 8 worker streams (largest first, to balance the bytes).  cuda_stream: the stream id_batch_run enqueues on (NULL = legacy
  * default stream).  Errors: ID_ERR_INVALID_ARG (NULL, count outside
  * [1, ID_BATCH_MAX_PROBLEMS], a problem out of its ranges), ID_ERR_OOM,
  * ID_ERR_CUDA. */
