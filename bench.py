@@ -482,16 +482,18 @@ def run_ours(args):
 
 # ------------------------------------------------------------ batched form
 
-def batched_problems(count=64, seed=1):
+def batched_problems(count=64, seed=1, max_rows=2_000_000):
     """Sizes of the batched workload: 64 channel fields of uneven size, m ~
     U[50k, 2M] rounded to 3 nx ny nz with nx = nz = 2 ny, n ~ U[64, 512],
-    k ~ U[10, 80], l = k + 10 (above 64, W in two passes of Psi rows), seeds
-    1..64, FP32 data, every other problem in the BF16 sketch form."""
+    k ~ U[10, 80], l = k + 10 (up to 90), seeds 1..64, FP32 data, every
+    other problem in the BF16 sketch form.  count and max_rows (m capped
+    before rounding) give smaller cases of the same mix, for profiling."""
     import numpy as np
     rng = np.random.default_rng(seed)
     out = []
     for b in range(count):
-        ny = max(2, int(round((rng.uniform(50_000, 2_000_000) / 12.0) ** (1.0 / 3.0))))
+        mrow = min(rng.uniform(50_000, 2_000_000), max_rows)
+        ny = max(2, int(round((mrow / 12.0) ** (1.0 / 3.0))))
         n = int(rng.integers(64, 513))
         k = int(rng.integers(10, 81))
         out.append(dict(grid=(2 * ny, ny, 2 * ny), n=n, k=k, l=k + 10, seed=b + 1,
@@ -508,7 +510,7 @@ def run_batched(args):
     lib = load()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    spec = batched_problems()
+    spec = batched_problems(args.batch_count, max_rows=args.batch_max_rows)
     probs, nbytes = [], 0
     for p in spec:
         A = channel_field(p["grid"], NCOMP, p["n"], seed=p["seed"], dtype=torch.float32,
@@ -549,18 +551,19 @@ def run_batched(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic channel fields (seeded), resident in HBM",
-        "config": {"workload": "64 channel fields of uneven size in one graph launch "
-                               "(one persistent work-list sketch launch, batched QRs): "
-                               "m ~ U[50k, 2M] (3 x 2ny x ny x 2ny), n ~ U[64, 512], "
-                               "k ~ U[10, 80], l = k + 10, seeds 1..64, FP32, "
+        "config": {"workload": f"{len(probs)} channel fields of uneven size in one graph launch "
+                               "(one persistent kernel: work-list sketches, each matrix's W "
+                               "sums, QR and solve by the CTA that completes it): "
+                               f"m ~ U[50k, {args.batch_max_rows / 1e6:g}M] (3 x 2ny x ny x 2ny), "
+                               "n ~ U[64, 512], "
+                               f"k ~ U[10, 80], l = k + 10, seeds 1..{len(probs)}, FP32, "
                                "every other problem BF16 sketch",
                    "problems": len(probs), "bytes_per_step": nbytes,
                    "m_range": [min(ms_), max(ms_)],
                    "n_range": [min(p["n"] for p in spec), max(p["n"] for p in spec)],
                    "k_range": [min(p["k"] for p in spec), max(p["k"] for p in spec)],
                    "l2": f"inputs larger than L2 ({nbytes / 1e9:.1f} GB); no flush needed"},
-        "roofline": {"kernel": "whole batch (one graph launch: work-list sketch, slab sums, "
-                               "QRs, solves)",
+        "roofline": {"kernel": "whole batch (one graph launch of one persistent kernel)",
                      "bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": "of " + kind,
                      "unit": "GB/s", "frac": gbs / peak, "traffic": None},
         "gpu_launches": launches, "clocks": clk,
@@ -745,6 +748,10 @@ def main():
     ap.add_argument("--prec", choices=["exact", "bf16"], default="exact",
                     help="sketch precision of the channel workload: FP32-accurate (default) "
                          "or the bfloat16 precision form")
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="batched workload: the first N problems of the mix (profiling)")
+    ap.add_argument("--batch-max-rows", type=int, default=2_000_000,
+                    help="batched workload: cap on each problem's rows (profiling)")
     ap.add_argument("--train-windows", type=int, default=200)
     ap.add_argument("--held-windows", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=4)

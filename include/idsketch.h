@@ -316,9 +316,11 @@ void id_batch_destroy(id_batch* b);
  * (0: the work list's bytes over 16 items per SM, between 4 and 64 MB);
  * without one, a problem's sketch runs on at most ceil(row blocks / c) CTAs
  * (0: one CTA per SM).  Outputs: choice (the chosen c, may be NULL), ms (the
- * 5 average replay times in candidate order, host, may be NULL).  The outputs J, P, kout hold
- * a complete result of the batch on return.  No counterpart in the paper.
- * Errors: as id_batch_run. */
+ * 5 average replay times in candidate order, host, may be NULL).  The
+ * outputs J, P, kout hold a complete result of the batch on return.  No
+ * counterpart in the paper.
+ * Errors: as id_batch_run, and ID_ERR_TIMEOUT (a device wait of some candidate
+ * gave up; poisoned). */
 id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout, int32_t* choice,
                         float* ms);
 

@@ -593,6 +593,18 @@ id_status id_batch_tune(id_batch* b, int32_t* J, double* P, int32_t* kout, int32
       break;
     }
     t /= 3.f;
+    // a candidate whose device waits gave up is an error, not a timing
+    std::vector<int> flags(b->prob.size());
+    e = cudaMemcpy(flags.data(), b->d_stat, sizeof(int) * flags.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      s = fail_cuda(b, e);
+      break;
+    }
+    if (std::any_of(flags.begin(), flags.end(), [](int f) { return f != 0; })) {
+      b->poisoned = true;
+      s = ID_ERR_TIMEOUT;
+      break;
+    }
     if (ms) ms[c] = t;
     if (c == 0 || t < best_ms) {
       best_ms = t;

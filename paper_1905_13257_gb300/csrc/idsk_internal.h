@@ -110,7 +110,8 @@ struct SketchArgs {
   void* Ac;             // mc x n_max, column-major, dtype
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
-  float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][64]
+  float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][w_width]
+  const uint8_t* rbflag;   // tensor-core kernel: per 128-row block, 1 if it holds coarse rows
   int32_t s0;           // first row of Psi drawn by this launch (a multiple of 10)
 };
 
@@ -263,6 +264,7 @@ struct id_sketch {
   double* d_W = nullptr;
   void* d_Y = nullptr;
   void* d_Ac = nullptr;
+  uint8_t* d_rbflag = nullptr;   // per 128-row block: holds coarse-grid rows (FP32, want_coarse)
 
   std::vector<idsk::Seg> pend;   // borrowed chunks, window-relative col0
   int64_t pend_cols = 0;
@@ -331,6 +333,8 @@ struct id_sketch {
 
 // ------------------------------------------------------------- launchers
 namespace idsk {
+// Flags of the 128-row blocks that hold coarse-grid rows (sketch_tc.cu).
+cudaError_t launch_coarse_flags(const CoarseGeom& g, int64_t m, uint8_t* flag, cudaStream_t st);
 cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64_t first,
                                  int64_t count, int width, const float* table, float* out,
                                  cudaStream_t st);

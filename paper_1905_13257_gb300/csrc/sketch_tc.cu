@@ -234,15 +234,10 @@ __device__ __forceinline__ Smem carve(uint32_t base) {
   return S;
 }
 
-// Barrier set of one row range (thread 0).  again: the barriers of the
-// previous range are invalidated first (every role has left them: the caller
-// synchronised the CTA, and every MMA and TMA copy they tracked completed).
+// The CTA's barrier set (thread 0, once per kernel).
 template <bool TMA>
-__device__ __forceinline__ void init_bars(const Smem& S, bool again) {
+__device__ __forceinline__ void init_bars(const Smem& S) {
   auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
-  if (again)
-    for (int i = 0; i < NBAR; ++i)
-      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar(i)) : "memory");
   mbar_init(bar(B_FULL0), NCONV);
   mbar_init(bar(B_FULL1), NCONV);
   mbar_init(bar(B_FREE0), 1);
@@ -269,6 +264,20 @@ __device__ __forceinline__ void init_bars(const Smem& S, bool again) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Running counts of each role across the row ranges that one CTA processes
+// (the persistent batched kernel runs many ranges with one barrier set, so
+// every barrier phase follows from these counts; a single range starts them
+// at zero).  A thread keeps only its own role's counts.
+struct RoleCounters {
+  int g = 0;           // row blocks (epilogue, MMA issuer)
+  int u = 0;           // bfloat16 piece units (TMA converters, MMA issuer)
+  int t = 0;           // tiles (register-form converters and MMA issuer)
+  int box = 0;         // raw TMA boxes (TMA converters, producer)
+  int done = 0;        // completed ranges (MMA issuer: phase of B_DONE)
+  uint32_t wpar = 0;   // per W^T tile: parity of its flushes (epilogue, MMA issuer)
+  uint32_t wpend = 0;  // MMA issuer: tiles handed to the epilogue, not yet read back
+};
+
 // The roles of one CTA over row blocks rb_begin .. rb_begin + nloc - 1 of
 // one window (ncols columns, the first of global index col_base), its W^T
 // partials into the FP32 slab `slab` ([nct * 128][64]).  tm: generic address
@@ -278,7 +287,8 @@ template <int NP, bool TMA, bool WY>
 __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* wp, int ncols,
                                              int64_t col_base, uint64_t tm, int64_t rb_begin,
                                              int nloc, float* slab, int drain_blocks,
-                                             const Smem& S, uint32_t tmem, uint8_t* smem_raw) {
+                                             const Smem& S, uint32_t tmem, uint8_t* smem_raw,
+                                             RoleCounters& rc) {
   auto bar = [&](int i) { return S.bars + 8u * (uint32_t)i; };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nct = (ncols + TCOLS - 1) / TCOLS;
@@ -314,13 +324,14 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     const int rq = (lane & 7) * 4;
     int64_t* rcs = reinterpret_cast<int64_t*>(smem_raw + (S.rc - smem_u32(smem_raw)));
     const uint8_t* rawp = smem_raw + (S.raw - smem_u32(smem_raw));
-    int t = 0;
+    int U = rc.u, X = rc.box;
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
       const int64_t rbase = (rb_begin + i) * TR;
-      // coarse-grid rows of this row block (most row blocks hold none)
+      // coarse-grid rows of this row block (most row blocks hold none: the
+      // per-block flag spares them the index arithmetic and both barriers)
       bool gather = false;
-      if (a.cg.on) {
+      if (a.cg.on && a.rbflag[rb_begin + i]) {
         asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
         int64_t rcv = -1;
         if (tid < TR) {
@@ -329,25 +340,23 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
         }
         gather = conv_bar_or(rcv >= 0);
       }
-      for (int ct = 0; ct < nct && ok; ++ct, ++t) {
-        // Piece units u = NP t + p take the two piece slots in turn (slot
-        // u & 1, its (u >> 1)-th use): with NP = 2 the MMAs of one piece run
-        // while the converters write the other.
-        const int u0 = NP * t, s0 = u0 & 1;
-        if ((u0 >> 1) >= 1 &&
-            !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag, 16)) {
+      for (int ct = 0; ct < nct && ok; ++ct, U += NP, X += 4) {
+        // Piece units u take the two piece slots in turn (slot u & 1, its
+        // (u >> 1)-th use): with NP = 2 the MMAs of one piece run while the
+        // converters write the other.
+        const int u0 = U, s0 = u0 & 1;
+        if (u0 >= 2 && !mbar_wait(bar(B_FREE0 + s0), ((u0 >> 1) - 1) & 1, S.abort_flag, 16)) {
           ok = false;
           break;
         }
-        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t);
+        if (warp == 0 && lane == 0) TC_TRACE(0, 4 * u0);
         const uint32_t hi_buf = S.pieces + (uint32_t)s0 * PIECE_BYTES;
         uint32_t lo_keep[NP > 1 ? 32 : 1];   // second piece, packed, until its slot frees
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int u = 4 * t + j, st = u % NST;
-          if (ok && !mbar_wait(bar(B_RF0 + st), (u / NST) & 1, S.abort_flag)) ok = false;
+          const int xb = X + j, st = xb % NST;
+          if (ok && !mbar_wait(bar(B_RF0 + st), (xb / NST) & 1, S.abort_flag)) ok = false;
           if (!ok) continue;
-          if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 1 + j);
           const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
           const int cc = 32 * j + cl;              // column inside the tile
           const int wc = ct * TCOLS + cc;          // column inside the window
@@ -377,29 +386,30 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_FULL0 + s0));
-        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 5);
+        if (warp == 0 && lane == 0) TC_TRACE(0, 4 * u0 + 1);
         if (NP > 1) {
-          const int u1 = u0 + 1;   // slot 1
-          if ((u1 >> 1) >= 1 &&
-              !mbar_wait(bar(B_FREE1), ((u1 >> 1) - 1) & 1, S.abort_flag, 16)) {
+          const int u1 = u0 + 1, s1 = u1 & 1;   // the other slot
+          if (u1 >= 2 && !mbar_wait(bar(B_FREE0 + s1), ((u1 >> 1) - 1) & 1, S.abort_flag, 16)) {
             ok = false;
             break;
           }
-          if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 6);
+          if (warp == 0 && lane == 0) TC_TRACE(0, 4 * u0 + 2);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int g = 0; g < 4; ++g)
-              st_shared_v2(S.pieces + PIECE_BYTES +
+              st_shared_v2(S.pieces + (uint32_t)s1 * PIECE_BYTES +
                                swz((uint32_t)(32 * j + cl), (uint32_t)(32 * g + rq), 2048u),
                            lo_keep[(j * 4 + g) * 2], lo_keep[(j * 4 + g) * 2 + 1]);
           fence_proxy_async();
           __syncwarp();
-          if (lane == 0) mbar_arrive(bar(B_FULL1));
+          if (lane == 0) mbar_arrive(bar(B_FULL0 + s1));
         }
-        if (warp == 0 && lane == 0) TC_TRACE(0, 8 * t + 7);
+        if (warp == 0 && lane == 0) TC_TRACE(0, 4 * u0 + 3);
       }
     }
+    rc.u = U;
+    rc.box = X;
     } else {
     // ------------------------------------------------------------ converters
     // A tile is two half tiles of 64 columns; each thread owns 8 columns x 4
@@ -411,7 +421,7 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     const bool one_seg = (w.nseg == 1);
     const float* seg_base = reinterpret_cast<const float*>(w.seg[0].ptr);
     const int64_t seg_ld = w.seg[0].ld;
-    int64_t rc[4] = {-1, -1, -1, -1};
+    int64_t rcx[4] = {-1, -1, -1, -1};
     auto load_half = [&](int64_t r0, int c0, float4 (&v)[8]) {
       const bool rows_ok = r0 + 3 < a.m;
 #pragma unroll
@@ -439,10 +449,10 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
         }
         if (a.cg.on && c0 + j < w.ncols) {
           float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + c0 + j);
-          if (rc[0] >= 0) Ac[rc[0]] = x.x;
-          if (rc[1] >= 0) Ac[rc[1]] = x.y;
-          if (rc[2] >= 0) Ac[rc[2]] = x.z;
-          if (rc[3] >= 0) Ac[rc[3]] = x.w;
+          if (rcx[0] >= 0) Ac[rcx[0]] = x.x;
+          if (rcx[1] >= 0) Ac[rcx[1]] = x.y;
+          if (rcx[2] >= 0) Ac[rcx[2]] = x.z;
+          if (rcx[3] >= 0) Ac[rcx[3]] = x.w;
         }
       }
     };
@@ -450,25 +460,27 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     const int c_hi = 64 + warp * 8;    // half 1 columns
     float4 bufA[8], bufB[8];
     if (ntile > 0) load_half(rb_begin * TR + row_off, c_lo, bufA);
-    int t = 0;
+    int tl = 0;   // tile index inside the range; rc.t + tl: the running count
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
       const int64_t r0 = (rb_begin + i) * TR + row_off;
       if (a.cg.on) {
+        const bool any = a.rbflag[rb_begin + i] != 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) rc[q] = (r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
+        for (int q = 0; q < 4; ++q)
+          rcx[q] = (any && r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
       }
-      for (int ct = 0; ct < nct; ++ct, ++t) {
+      for (int ct = 0; ct < nct; ++ct, ++tl) {
         const int cbase = ct * TCOLS;
         load_half(r0, cbase + c_hi, bufB);                       // half 1 of this tile
-        const int b = t & 1;
+        const int t = rc.t + tl, b = t & 1;
         if (t >= 2 && !mbar_wait(bar(B_FREE0 + b), ((t >> 1) - 1) & 1, S.abort_flag)) {
           ok = false;
           break;
         }
         const uint32_t pbuf = S.pieces + (uint32_t)b * NP * PIECE_BYTES;
         store_half(pbuf, r0, cbase + c_lo, c_lo, bufA);          // half 0
-        if (t + 1 < ntile) {                                      // half 0 of the next tile
+        if (tl + 1 < ntile) {                                     // half 0 of the next tile
           const bool last_ct = (ct + 1 == nct);
           load_half(last_ct ? r0 + TR : r0, last_ct ? c_lo : cbase + TCOLS + c_lo, bufA);
         }
@@ -479,13 +491,22 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
         if (warp == 0 && lane == 0) TC_TRACE(0, t);
       }
     }
+    rc.t += ntile;
     }
   } else if (warp < MMA_WARP) {
     // -------------------------------------------------------------- epilogue
     const int q = warp - NCONV;           // TMEM lane quarter
     const int rl = q * 32 + lane;         // row (Y) / column (W^T) inside the tile
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    auto gen_psi = [&](int i, int pb) {
+    const int g0 = rc.g;   // running row-block count: Psi buffer and Y accumulator phases
+    // Psi of row block i of the range into buffer (g0 + i) mod npsi, once
+    // the MMAs of the row block npsi earlier (maybe of an earlier range)
+    // have completed; false when the wait gave up
+    auto gen_psi = [&](int i) {
+      const int g = g0 + i, pb = g & (npsi - 1);
+      if (g >= npsi &&
+          !mbar_wait(bar(B_PSIE0 + pb), ((g / npsi) - 1) & 1, S.abort_flag, 256))
+        return false;
       const int64_t r = (rb_begin + i) * TR + rl;
       const uint32_t dst = psi0 + (uint32_t)pb * psi_bytes;
       if (WY || lw == 64)
@@ -495,11 +516,13 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_PSIF0 + pb));
+      return true;
     };
-    for (int i = 0; i < npsi && i < nloc; ++i) gen_psi(i, i);
-    uint32_t wpar = 0, wseen = 0;   // per W^T tile: flush-count parity, flushed before
-    for (int i = 0; i < nloc; ++i) {
-      const int pb = i & (npsi - 1), yb = i & 1;
+    bool pok = true;
+    for (int i = 0; i < npsi && i < nloc && pok; ++i) pok = gen_psi(i);
+    uint32_t wpar = rc.wpar, wseen = 0;   // per W^T tile: flush parity, flushed in this range
+    for (int i = 0; i < nloc && pok; ++i) {
+      const int g = g0 + i, yb = g & 1;
       // a later window adds into Y: its old values of row block i + 2 are
       // prefetched into L2 now (the warp's 32 rows of every sketch column),
       // so that the read-modify-write at the drain waits for L2, not HBM
@@ -565,7 +588,7 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
       if (!wok) break;
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i);
       if (wy) {   // Y of row block i: accumulator yb
-        if (!mbar_wait(bar(B_YF0 + yb), (i >> 1) & 1, S.abort_flag, 256)) break;
+        if (!mbar_wait(bar(B_YF0 + yb), (g >> 1) & 1, S.abort_flag, 256)) break;
         tc_fence_after();
         if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 1);
         const int64_t r = (rb_begin + i) * TR + rl;
@@ -594,28 +617,27 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
         if (lane == 0) mbar_arrive(bar(B_YE0 + yb));
       }
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 2);
-      if (i + npsi < nloc) {   // Psi buffer pb is free once row block i's MMAs completed
-        if (!mbar_wait(bar(B_PSIE0 + pb), (i / npsi) & 1, S.abort_flag, 256)) break;
-        gen_psi(i + npsi, pb);
-      }
+      if (i + npsi < nloc && !gen_psi(i + npsi)) break;   // into row block i's buffer
       if (q == 0 && lane == 0) TC_TRACE(2, 4 * i + 3);
     }
+    rc.g = g0 + nloc;
+    rc.wpar = wpar;
   } else if (warp == MMA_WARP && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    uint32_t accw = 0;    // bit ct: W^T accumulator of tile ct holds data
-    uint32_t wpend = 0;   // bit ct: tile ct handed to the epilogue, not yet read out
-    uint32_t wpar = 0;    // bit ct: parity of the flushes of tile ct handed out
+    uint32_t accw = 0;          // bit ct: W^T accumulator of tile ct holds data
+    uint32_t wpend = rc.wpend;  // bit ct: tile ct handed to the epilogue, not yet read out
+    uint32_t wpar = rc.wpar;    // bit ct: parity of the flushes of tile ct handed out
     const uint32_t idesc_w = lw == 96 ? IDESC_W96 : IDESC_W;
-    int t = 0;
+    int t = rc.t, U = rc.u;
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
-      const int pb = i & (npsi - 1), yb = i & 1;
-      if (!mbar_wait(bar(B_PSIF0 + pb), (i / npsi) & 1, S.abort_flag)) break;
-      if (wy && i >= 2 && !mbar_wait(bar(B_YE0 + yb), ((i >> 1) - 1) & 1, S.abort_flag)) break;
+      const int g = rc.g + i, pb = g & (npsi - 1), yb = g & 1;
+      if (!mbar_wait(bar(B_PSIF0 + pb), (g / npsi) & 1, S.abort_flag)) break;
+      if (wy && g >= 2 && !mbar_wait(bar(B_YE0 + yb), ((g >> 1) - 1) & 1, S.abort_flag)) break;
       tc_fence_after();
       const uint32_t psi_s = psi0 + (uint32_t)pb * psi_bytes;
       const uint32_t ytm = tmem + (uint32_t)(TMEM_Y + yb * LP);
-      for (int ct = 0; ct < nct; ++ct, ++t) {
+      for (int ct = 0; ct < nct; ++ct, ++t, U += NP) {
         const int b = t & 1;
         if (!TMA && !mbar_wait(bar(B_FULL0 + b), (t >> 1) & 1, S.abort_flag)) {
           ok = false;
@@ -635,7 +657,7 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           uint32_t pa = pbuf + (uint32_t)p * PIECE_BYTES;
-          const int u = NP * t + p;   // TMA form: piece unit u in slot u & 1
+          const int u = U + p;   // TMA form: piece unit u in slot u & 1
           if (TMA) {   // the MMA thread is on the critical path: poll without sleeping
             if (!mbar_wait_spin(bar(B_FULL0 + (u & 1)), (u >> 1) & 1, S.abort_flag)) {
               ok = false;
@@ -683,19 +705,26 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
       if (wy) mma_commit(bar(B_YF0 + yb));
       mma_commit(bar(B_PSIE0 + pb));
     }
-    // every issued MMA has completed before the TMEM is released
+    // every issued MMA has completed before the range ends (the TMEM is
+    // released, or the next range overwrites the accumulators)
     mma_commit(bar(B_DONE));
     const long long t0 = clock64();
-    while (!mbar_try(bar(B_DONE), 0)) {
+    while (!mbar_try(bar(B_DONE), rc.done & 1)) {
       if (clock64() - t0 > kWaitCycles) {
         st_volatile_shared(S.abort_flag, 1);
         break;
       }
     }
+    rc.done += 1;
+    rc.g += nloc;
+    rc.t = t;
+    rc.u = U;
+    rc.wpar = wpar;
+    rc.wpend = wpend;
   } else if (TMA && warp == PROD_WARP && lane == 0) {
     // -------------------------------------------------------- TMA producer
     const uint64_t stream_once = policy_evict_first();
-    int u = 0;
+    int u = rc.box;
     bool ok = true;
     for (int t = 0; t < ntile && ok; ++t) {
       const int i = t / nct, ct = t - i * nct;
@@ -712,6 +741,7 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
                     bar(B_RF0 + st), stream_once);
       }
     }
+    rc.box = u;
   }
 }
 
@@ -759,7 +789,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   const int64_t rb_end = nrb * (blockIdx.x + 1) / gridDim.x;
   if (tid == 0) {
     st_volatile_shared(S.abort_flag, 0);
-    init_bars<TMA>(S, false);
+    init_bars<TMA>(S);
   }
   if (WY) fill_omega<TMA>(S, a, w.ncols, w.col_base);
   if (warp == MMA_WARP) tmem_alloc_all(S);
@@ -769,12 +799,12 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   tc_fence_after();
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
+  RoleCounters rc;
   sketch_roles<NP, TMA, WY>(a, &w, w.ncols, w.col_base, reinterpret_cast<uint64_t>(&tmap), rb_begin,
-                        (int)(rb_end - rb_begin),
-                        a.wpart + (int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) *
-                                      w_width(a.l, a.want_Y != 0),
-                        drain_blocks,
-                        S, tmem, smem_raw);
+                            (int)(rb_end - rb_begin),
+                            a.wpart + (int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) *
+                                          w_width(a.l, a.want_Y != 0),
+                            drain_blocks, S, tmem, smem_raw, rc);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -822,11 +852,14 @@ __device__ __forceinline__ void finish_job(const BatchJob& jb, const BatchItem* 
 // Batched form in one persistent launch: a work list of row ranges (items)
 // over the sketches (jobs) of many matrices, one CTA per SM.  A CTA takes the
 // next item from a global counter (jobs in order of decreasing QR work, each
-// job's items in row order), sets up the job's arguments and a fresh barrier
-// set, runs the roles over the item's row blocks into the item's W^T slab,
-// and synchronises.  The CTA that completes a job's last item (counted per
-// job after its slab writes are fenced) sums the job's slabs into W and runs
-// its pivoted QR and solve, while the other CTAs go on with later items.  The
+// job's items in row order), copies the job's arguments to shared memory,
+// runs the roles over the item's row blocks into the item's W^T slab, and
+// synchronises.  One barrier set serves all items: every role carries its
+// running counts (RoleCounters) from item to item, so each wait expects the
+// right phase, including the commits of an earlier item that nobody waited
+// for inside it.  The CTA that completes a job's last item (counted per job
+// after its slab writes are fenced) sums the job's slabs into W and runs its
+// pivoted QR and solve, while the other CTAs go on with later items.  The
 // TMEM stays allocated throughout.  Every wait stays bounded: a CTA that
 // gives up raises its job's problem flag and stops taking items.
 __global__ void __launch_bounds__(NTHREADS_TMA, 1)
@@ -845,14 +878,18 @@ __global__ void __launch_bounds__(NTHREADS_TMA, 1)
   uint8_t* scratch = smem_raw + (S.pieces - sbase);   // free between items
   int* job_done = counters + 1;
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (tid == 0) st_volatile_shared(S.abort_flag, 0);
+  if (tid == 0) {
+    st_volatile_shared(S.abort_flag, 0);
+    init_bars<true>(S);   // one barrier set for all ranges: phases follow the counters
+  }
   if (warp == MMA_WARP) tmem_alloc_all(S);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
-  for (int round = 0;; ++round) {
+  RoleCounters rc;
+  for (;;) {
     if (tid == 0) {
       const int q = atomicAdd(counters, 1);
       st_volatile_shared(s_item, q < nitems ? order[q] : -1);
@@ -866,17 +903,16 @@ __global__ void __launch_bounds__(NTHREADS_TMA, 1)
       const uint32_t* src = reinterpret_cast<const uint32_t*>(&jb.a);
       uint32_t* dst = reinterpret_cast<uint32_t*>(args);
       for (int e = tid; e < (int)(sizeof(SketchArgs) / 4); e += NTHREADS_TMA) dst[e] = src[e];
-      if (tid == 0) init_bars<true>(S, round > 0);
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
       const uint64_t tm = reinterpret_cast<uint64_t>(tmaps + item.job);
       if (jb.np == 2)
         sketch_roles<2, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
-                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw);
+                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw, rc);
       else
         sketch_roles<1, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
-                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw);
+                                     slabs + item.slab, drain_blocks, S, tmem, smem_raw, rc);
     }
     if (warp >= NCONV && warp < MMA_WARP) __threadfence();   // the slab writes, GPU-wide
     tc_fence_before();
@@ -970,11 +1006,11 @@ cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int d
 
 #ifdef IDSK_TC_TRACE
 // Profiling harness only: the clock64 timeline of CTA 0 ([4][8192]): role 0
-// converter warp 0 (per tile t: 8t start, 8t+1+j box j in, 8t+5 first piece
-// out, 8t+6 second slot free, 8t+7 second piece out), role 1 MMA (2u piece
-// unit u ready, 2u+1 issued), role 2 epilogue (per row block i: 4i flushes
-// done, 4i+1 Y ready, 4i+2 Y drained, 4i+3 Psi drawn), role 3 producer (box u
-// issued).
+// converter warp 0 (per tile with first piece unit u: 4u start, 4u+1 first
+// piece out, 4u+2 second slot free, 4u+3 second piece out), role 1 MMA (2u
+// piece unit u ready, 2u+1 issued), role 2 epilogue (per row block i: 4i
+// flushes done, 4i+1 Y ready, 4i+2 Y drained, 4i+3 Psi drawn), role 3
+// producer (box u issued).
 extern "C" int idsk_tc_trace_read(long long* host) {
   return (int)cudaMemcpyFromSymbol(host, g_tc_trace, sizeof(g_tc_trace));
 }
@@ -1033,6 +1069,21 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(
       a.wpart, grid, a.l, w_width(a.l, a.want_Y != 0), w.ncols, nrb, a.W, a.ldw, w.col_base);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void coarse_flags_kernel(CoarseGeom g, int64_t m, uint8_t* __restrict__ flag) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m && coarse_index_tc(r, g) >= 0) flag[r / TR] = 1;
+}
+}  // namespace
+
+cudaError_t launch_coarse_flags(const CoarseGeom& g, int64_t m, uint8_t* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)((m + TR - 1) / TR), st);
+  if (e != cudaSuccess) return e;
+  coarse_flags_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, m, flag);
+  count_launches(1);
   return cudaGetLastError();
 }
 
