@@ -91,7 +91,7 @@ void free_all(id_sketch* h) {
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gvec, h->d_hvec, h->d_vh, h->d_vl,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
                   h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart,
-                  h->d_axis, h->d_Sc, h->d_cand, h->d_fq, h->d_rbflag};
+                  h->d_axis, h->d_Sc, h->d_cand, h->d_fq, h->d_crow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -207,7 +207,7 @@ id_status launch_pending(id_sketch* h) {
     a.cg = h->cg;
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
     a.wpart = h->d_wpart;
-    a.rbflag = h->d_rbflag;
+    a.crow = h->d_crow;
     const int nsm_eff = h->grid_cap > 0 ? std::min(h->grid_cap, h->nsm) : h->nsm;
     if (tc) {
       IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, nsm_eff, h->drain_blocks, h->d_status,
@@ -389,7 +389,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   al.get(&h->d_W, (size_t)l * nm);
   if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);
   if (cfg->want_coarse) al.get((char**)&h->d_Ac, (size_t)h->mc * nm * h->esz);
-  if (cfg->want_coarse && cfg->dtype == ID_F32) al.get(&h->d_rbflag, (size_t)(h->m + 127) / 128);
+  if (cfg->want_coarse && cfg->dtype == ID_F32) al.get(&h->d_crow, (size_t)h->mc);
   al.get(&h->d_work, (size_t)l * nm);
   al.get(&h->d_R, (size_t)k * nm);
   al.get(&h->d_P, (size_t)k * nm);
@@ -430,7 +430,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
                                        h->d_omega, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_W, 0, sizeof(double) * l * nm, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st);
-  if (e == cudaSuccess && h->d_rbflag) e = launch_coarse_flags(h->cg, h->m, h->d_rbflag, h->st);
+  if (e == cudaSuccess && h->d_crow) e = launch_coarse_rows(h->cg, h->m, h->d_crow, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e == cudaSuccess && cfg->want_coarse && cfg->dtype == ID_F32 &&
       !getenv("IDSKETCH_NO_SIDE_STREAM")) {

@@ -111,7 +111,7 @@ struct SketchArgs {
   CoarseGeom cg;
   int32_t bf16;         // round A to bfloat16 before the products
   float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][w_width]
-  const uint8_t* rbflag;   // tensor-core kernel: per 128-row block, 1 if it holds coarse rows
+  const int64_t* crow;  // tensor-core path: fine row of each coarse row (the A_c copy)
   int32_t s0;           // first row of Psi drawn by this launch (a multiple of 10)
 };
 
@@ -264,7 +264,7 @@ struct id_sketch {
   double* d_W = nullptr;
   void* d_Y = nullptr;
   void* d_Ac = nullptr;
-  uint8_t* d_rbflag = nullptr;   // per 128-row block: holds coarse-grid rows (FP32, want_coarse)
+  int64_t* d_crow = nullptr;   // fine row of each coarse-grid row (FP32, want_coarse)
 
   std::vector<idsk::Seg> pend;   // borrowed chunks, window-relative col0
   int64_t pend_cols = 0;
@@ -333,8 +333,12 @@ struct id_sketch {
 
 // ------------------------------------------------------------- launchers
 namespace idsk {
-// Flags of the 128-row blocks that hold coarse-grid rows (sketch_tc.cu).
-cudaError_t launch_coarse_flags(const CoarseGeom& g, int64_t m, uint8_t* flag, cudaStream_t st);
+// The coarse rows of the tensor-core path (sketch_tc.cu): crow[coarse index]
+// = fine row, once per handle; A_c(:, window) = A(crow, window) after each
+// window's sketch.
+cudaError_t launch_coarse_rows(const CoarseGeom& g, int64_t m, int64_t* crow, cudaStream_t st);
+cudaError_t launch_coarse_gather(const Window& w, const int64_t* crow, int64_t mc, float* Ac,
+                                 cudaStream_t st);
 cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64_t first,
                                  int64_t count, int width, const float* table, float* out,
                                  cudaStream_t st);

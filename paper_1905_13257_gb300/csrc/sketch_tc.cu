@@ -2,9 +2,16 @@
 //
 // One read of each 128 x 128 tile of A forms both randomized sketches of the
 // window's columns (Algorithm 4 step 3, transposed orientation; eq.
-// eq:sampmatrix) and gathers the coarse-grid rows of Algorithm 5 step 3:
+// eq:sampmatrix):
 //   W^T(c, :) += A(R, c)^T Psi(:, R)^T   (128 columns x 64, TMEM accumulator)
 //   Y(R, :)   += A(R, C) Omega(C, :)     (128 rows x 64, TMEM accumulator)
+// The coarse-grid rows of Algorithm 5 step 3 are copied to A_c by a small
+// kernel right after each window's sketch (coarse_gather_kernel): it reads
+// only the row blocks that hold coarse rows (1/16 of A on a grid with
+// stride 4 in y and z).  Copied inside this kernel they cost far more: by
+// the converters 0.45 ms per 512-column window of 4.7M rows (their loop on
+// the critical path), by a dedicated warp 2.1 ms (the raw ring waits for
+// it), against 2.1 ms for the whole window without them.
 //
 // Precision.  A (FP32) is split once per tile into NP bfloat16 pieces,
 // A = a0 + a1 (+ rounding below 2^-16 |A|); Psi and Omega are exact in
@@ -27,7 +34,7 @@
 //   warps 0-7    converters: load A with 128-bit coalesced loads in half
 //                tiles (two register buffers: one half tile in flight),
 //                split into pieces, store them to the swizzled piece buffer
-//                (double-buffered), gather coarse rows
+//                (double-buffered)
 //   warps 8-11   epilogue: draw Psi for upcoming row blocks (counter
 //                generator), drain Y to global memory, flush W^T partials
 //                into a per-CTA FP32 slab in L2 (one 128-column tile at a
@@ -106,7 +113,6 @@ enum { B_FULL0 = 0, B_FULL1, B_FREE0, B_FREE1, B_PSIF0, B_PSIE0 = B_PSIF0 + 4,
 struct Smem {
   uint32_t pieces;   // [2 buffers][NP][PIECE_BYTES] (TMA form: [2 slots][PIECE_BYTES])
   uint32_t raw;      // TMA form: [NST][RAW_BYTES]
-  uint32_t rc;       // TMA form: coarse index of the 128 rows of the row block
   uint32_t omega;    // [kTcMaxTiles][OMEGA_TILE_BYTES]
   uint32_t psi;      // [2][PSI_BYTES]
   uint32_t bars;     // NBAR x 8 bytes
@@ -125,35 +131,6 @@ __device__ __forceinline__ void red_add_v4_f32(float* p, float a, float b, float
   asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
                "f"(a), "f"(b), "f"(c), "f"(d), "l"(policy)
                : "memory");
-}
-
-// Named barrier 1 over the converter warps that also ORs a predicate.
-__device__ __forceinline__ bool conv_bar_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(NCONV * 32)
-      : "memory");
-  return r != 0;
-}
-
-// Coarse rows of one raw column (128 rows in shared memory): this thread's
-// rows rq + 32 g + q (g, q < 4) whose coarse index is set go to A_c.  Only
-// row blocks that hold coarse rows come here; the loop stays rolled and out
-// of line because the converters' unrolled loop must fit the instruction
-// cache (inlined, the gather made the kernel 17% larger and 42% slower).
-__device__ __noinline__ void gather_column(const float* col, const int64_t* rcs, int rq,
-                                           float* Ac) {
-#pragma unroll 1
-  for (int g = 0; g < 4; ++g)
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const int rr = 32 * g + rq + q;
-      const int64_t rcv = rcs[rr];
-      if (rcv >= 0) Ac[rcv] = col[rr];
-    }
 }
 
 __device__ __forceinline__ int64_t coarse_index_tc(int64_t r, const CoarseGeom& g) {
@@ -227,8 +204,7 @@ __device__ __forceinline__ Smem carve(uint32_t base) {
   S.omega = S.pieces + (TMA ? 2u : 2u * NP) * PIECE_BYTES;
   S.psi = S.omega + kTcMaxTiles * OMEGA_TILE_BYTES;
   S.raw = S.psi + 2u * PSI_BYTES;
-  S.rc = S.raw + (TMA ? NST * RAW_BYTES : 0u);
-  S.bars = S.rc + (TMA ? TR * 8u : 0u);
+  S.bars = S.raw + (TMA ? NST * RAW_BYTES : 0u);
   S.tmem_slot = S.bars + NBAR * 8u;
   S.abort_flag = S.tmem_slot + 4u;
   return S;
@@ -279,13 +255,13 @@ struct RoleCounters {
 };
 
 // The roles of one CTA over row blocks rb_begin .. rb_begin + nloc - 1 of
-// one window (ncols columns, the first of global index col_base), its W^T
+// one window (ncols columns), its W^T
 // partials into the FP32 slab `slab` ([nct * 128][64]).  tm: generic address
 // of the window's tensor map (TMA form); w: the window's segments (register
 // form only).
 template <int NP, bool TMA, bool WY>
 __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* wp, int ncols,
-                                             int64_t col_base, uint64_t tm, int64_t rb_begin,
+                                             uint64_t tm, int64_t rb_begin,
                                              int nloc, float* slab, int drain_blocks,
                                              const Smem& S, uint32_t tmem, uint8_t* smem_raw,
                                              RoleCounters& rc) {
@@ -322,24 +298,10 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     // disjoint 16-byte chunk positions for rows 0-31).
     const int cl = (warp >> 1) * 8 + (warp & 1) * 2 + ((lane >> 3) & 1) * 4 + (lane >> 4);
     const int rq = (lane & 7) * 4;
-    int64_t* rcs = reinterpret_cast<int64_t*>(smem_raw + (S.rc - smem_u32(smem_raw)));
     const uint8_t* rawp = smem_raw + (S.raw - smem_u32(smem_raw));
     int U = rc.u, X = rc.box;
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
-      const int64_t rbase = (rb_begin + i) * TR;
-      // coarse-grid rows of this row block (most row blocks hold none: the
-      // per-block flag spares them the index arithmetic and both barriers)
-      bool gather = false;
-      if (a.cg.on && a.rbflag[rb_begin + i]) {
-        asm volatile("bar.sync 1, %0;" ::"n"(NCONV * 32) : "memory");
-        int64_t rcv = -1;
-        if (tid < TR) {
-          rcv = (rbase + tid < a.m) ? coarse_index_tc(rbase + tid, a.cg) : -1;
-          rcs[tid] = rcv;
-        }
-        gather = conv_bar_or(rcv >= 0);
-      }
       for (int ct = 0; ct < nct && ok; ++ct, U += NP, X += 4) {
         // Piece units u take the two piece slots in turn (slot u & 1, its
         // (u >> 1)-th use): with NP = 2 the MMAs of one piece run while the
@@ -359,7 +321,6 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
           if (!ok) continue;
           const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
           const int cc = 32 * j + cl;              // column inside the tile
-          const int wc = ct * TCOLS + cc;          // column inside the window
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int rr = 32 * g + rq;
@@ -376,9 +337,6 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
               lo_keep[(j * 4 + g) * 2 + 1] = pack_bf16x2(x.z - f23.x, x.w - f23.y);
             }
           }
-          if (gather && wc < ncols)
-            gather_column(raw + cl * TR, rcs, rq,
-                          reinterpret_cast<float*>(a.Ac) + a.cg.mc * (col_base + wc));
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(B_RE0 + st));
         }
@@ -421,7 +379,6 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     const bool one_seg = (w.nseg == 1);
     const float* seg_base = reinterpret_cast<const float*>(w.seg[0].ptr);
     const int64_t seg_ld = w.seg[0].ld;
-    int64_t rcx[4] = {-1, -1, -1, -1};
     auto load_half = [&](int64_t r0, int c0, float4 (&v)[8]) {
       const bool rows_ok = r0 + 3 < a.m;
 #pragma unroll
@@ -447,13 +404,6 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
           st_shared_v2(pbuf + PIECE_BYTES + off, pack_bf16x2(x.x - f01.x, x.y - f01.y),
                        pack_bf16x2(x.z - f23.x, x.w - f23.y));
         }
-        if (a.cg.on && c0 + j < w.ncols) {
-          float* Ac = reinterpret_cast<float*>(a.Ac) + a.cg.mc * (w.col_base + c0 + j);
-          if (rcx[0] >= 0) Ac[rcx[0]] = x.x;
-          if (rcx[1] >= 0) Ac[rcx[1]] = x.y;
-          if (rcx[2] >= 0) Ac[rcx[2]] = x.z;
-          if (rcx[3] >= 0) Ac[rcx[3]] = x.w;
-        }
       }
     };
     const int c_lo = warp * 8;         // half 0 columns of this warp
@@ -464,12 +414,6 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
     bool ok = true;
     for (int i = 0; i < nloc && ok; ++i) {
       const int64_t r0 = (rb_begin + i) * TR + row_off;
-      if (a.cg.on) {
-        const bool any = a.rbflag[rb_begin + i] != 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          rcx[q] = (any && r0 + q < a.m) ? coarse_index_tc(r0 + q, a.cg) : -1;
-      }
       for (int ct = 0; ct < nct; ++ct, ++tl) {
         const int cbase = ct * TCOLS;
         load_half(r0, cbase + c_hi, bufB);                       // half 1 of this tile
@@ -800,7 +744,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
   RoleCounters rc;
-  sketch_roles<NP, TMA, WY>(a, &w, w.ncols, w.col_base, reinterpret_cast<uint64_t>(&tmap), rb_begin,
+  sketch_roles<NP, TMA, WY>(a, &w, w.ncols, reinterpret_cast<uint64_t>(&tmap), rb_begin,
                             (int)(rb_end - rb_begin),
                             a.wpart + (int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) *
                                           w_width(a.l, a.want_Y != 0),
@@ -908,10 +852,10 @@ __global__ void __launch_bounds__(NTHREADS_TMA, 1)
       tc_fence_after();
       const uint64_t tm = reinterpret_cast<uint64_t>(tmaps + item.job);
       if (jb.np == 2)
-        sketch_roles<2, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
+        sketch_roles<2, true, false>(*args, nullptr, jb.ncols, tm, item.rb0, item.nrb,
                                      slabs + item.slab, drain_blocks, S, tmem, smem_raw, rc);
       else
-        sketch_roles<1, true, false>(*args, nullptr, jb.ncols, 0, tm, item.rb0, item.nrb,
+        sketch_roles<1, true, false>(*args, nullptr, jb.ncols, tm, item.rb0, item.nrb,
                                      slabs + item.slab, drain_blocks, S, tmem, smem_raw, rc);
     }
     if (warp >= NCONV && warp < MMA_WARP) __threadfence();   // the slab writes, GPU-wide
@@ -974,7 +918,7 @@ __global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, 
 template <int NP, bool TMA>
 size_t tc_smem_bytes() {
   return 1024 + (TMA ? 2u : 2u * NP) * PIECE_BYTES + kTcMaxTiles * OMEGA_TILE_BYTES +
-         2u * PSI_BYTES + (TMA ? NST * RAW_BYTES + TR * 8u : 0u) + NBAR * 8 + 16;
+         2u * PSI_BYTES + (TMA ? NST * RAW_BYTES : 0u) + NBAR * 8 + 16;
 }
 
 // Tensor map of the window's single segment: rows x columns FP32, boxes of
@@ -1069,20 +1013,45 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(
       a.wpart, grid, a.l, w_width(a.l, a.want_Y != 0), w.ncols, nrb, a.W, a.ldw, w.col_base);
   count_launches(2);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.cg.on) e = launch_coarse_gather(w, a.crow, a.cg.mc, reinterpret_cast<float*>(a.Ac), st);
+  return e;
 }
 
 namespace {
-__global__ void coarse_flags_kernel(CoarseGeom g, int64_t m, uint8_t* __restrict__ flag) {
+// The fine row of every coarse-grid row: crow[coarse_index(r)] = r.
+__global__ void coarse_rows_kernel(CoarseGeom g, int64_t m, int64_t* __restrict__ crow) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < m && coarse_index_tc(r, g) >= 0) flag[r / TR] = 1;
+  if (r >= m) return;
+  const int64_t rc = coarse_index_tc(r, g);
+  if (rc >= 0) crow[rc] = r;
+}
+
+// A_c(:, window) = A(crow, window) (Algorithm 5 step 3), exact FP32, right
+// after the window's sketch while its columns are still the caller's:
+// blockIdx.y = column of the window, threads over the coarse rows.
+__global__ void coarse_gather_kernel(const __grid_constant__ Window w,
+                                     const int64_t* __restrict__ crow, int64_t mc,
+                                     float* __restrict__ Ac) {
+  const int c = blockIdx.y;
+  const int64_t rc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rc >= mc) return;
+  const float* col = column_ptr(w, c);
+  Ac[(w.col_base + c) * mc + rc] = col[crow[rc]];
 }
 }  // namespace
 
-cudaError_t launch_coarse_flags(const CoarseGeom& g, int64_t m, uint8_t* flag, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)((m + TR - 1) / TR), st);
-  if (e != cudaSuccess) return e;
-  coarse_flags_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, m, flag);
+cudaError_t launch_coarse_rows(const CoarseGeom& g, int64_t m, int64_t* crow, cudaStream_t st) {
+  coarse_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, m, crow);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_gather(const Window& w, const int64_t* crow, int64_t mc, float* Ac,
+                                 cudaStream_t st) {
+  if (w.ncols <= 0 || mc <= 0) return cudaSuccess;
+  coarse_gather_kernel<<<dim3((unsigned)((mc + 255) / 256), (unsigned)w.ncols), 256, 0, st>>>(
+      w, crow, mc, Ac);
   count_launches(1);
   return cudaGetLastError();
 }
