@@ -796,7 +796,10 @@ cudaError_t launch_coarse_coop(id_sketch* h, int64_t n64, cudaStream_t st, int m
     l2 = 0;
   }
   // about 3/8 of L2 holds the leading columns of A_c from one step to the next
-  a.keep_cols = (int)std::min<int64_t>(n, (int64_t)(0.375 * l2 / (4.0 * (double)h->mc)));
+  double keep = 0.375;
+  if (const char* env = getenv("IDSKETCH_COARSE_L2_KEEP")) keep = atof(env);
+  a.keep_cols = (int)std::min<int64_t>(
+      n, (int64_t)(std::max(0.0, std::min(1.0, keep)) * l2 / (4.0 * (double)h->mc)));
   cudaError_t e = cudaMemsetAsync(h->d_cint, 0, 8 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
