@@ -435,6 +435,14 @@ def run_ours(args):
 
         e2e_run(max(1, args.warmup))
         torch.cuda.synchronize()
+        # the host link's own rate at this moment (one chunk, outside the
+        # timed region): it bounds e2e, and it has varied between calls
+        p0, p1 = ev(), ev()
+        p0.record(stream)
+        bufs[0][:, :CHUNK].copy_(A_host_v[:, :CHUNK], non_blocking=True)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        h2d_probe = 4.0 * m * CHUNK / (p0.elapsed_time(p1) / 1e3) / 1e9
         s0, s1 = ev(), ev()
         s0.record(stream)
         J, P, Jc, Pc = e2e_run(args.steps)
@@ -446,7 +454,8 @@ def run_ours(args):
                "h2d_bytes_per_step": 4 * m * n, "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms,
                "overlap": "host-to-device copies of step k + 1 under the compute of step k",
-               "host_numa_node": numa[0] if numa else None}
+               "host_numa_node": numa[0] if numa else None,
+               "h2d_probe_gbs": h2d_probe}
         del A_host, bufs
 
     cpu = None
