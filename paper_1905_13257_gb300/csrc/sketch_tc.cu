@@ -168,16 +168,20 @@ __device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window
   return y;
 }
 
-// Psi(0 .. LWT-1, r) of row r into column rl of a K-major Psi tile (zero
-// past l and past the last row).  The loop over groups of ten stays rolled:
+// Psi(0 .. l-1, r) of row r into column rl of a K-major Psi tile (zero past
+// the last row), in groups of ten draws: only the ceil(l / 10) groups that
+// hold rows below l are drawn.  The tile's rows from there to LWT - 1 keep
+// whatever they hold; they only feed the W^T accumulator columns past l,
+// which no sum reads.  The loop over the groups stays rolled:
 // unrolled, the longer epilogue code made the sketch slower for every n but
 // the smallest (measured: 2.64 against 2.76 ms per launch with Y; 1.75
 // against 1.77 us per tile at n = 512 without Y; 3.16 against 2.73 us at
 // n = 64, one 128-column tile per row block).
 template <int LWT>
 __device__ __forceinline__ void psi_row(const SketchArgs& a, int64_t r, int rl, uint32_t dst) {
+  const int ngroups = (min(a.l, LWT) + 9) / 10;
 #pragma unroll 1
-  for (int sb = 0; sb * 10 < LWT; ++sb) {
+  for (int sb = 0; sb < ngroups; ++sb) {
     float g[10];
     if (r < a.m) {
       gauss10((uint64_t)r, (uint32_t)(sb + a.s0 / 10), kStreamPsi, a.k0, a.k1, a.table, g);
