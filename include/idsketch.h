@@ -77,7 +77,7 @@ typedef struct {
   int32_t ncomp;           /* velocity components; grid/ncomp unused if 0       */
   int32_t coarse_stride[3];/* sx, sy, sz of the coarse grid (direct injection)  */
   int32_t want_Y;          /* 1: also form Y = A Omega (m x l)                  */
-  int32_t want_coarse;     /* 1: gather A_c = A(rows_c, :) during the pass      */
+  int32_t want_coarse;     /* 1: copy A_c = A(rows_c, :) window by window        */
   int32_t window_cols;     /* columns aggregated per launch; 0 = process every
                               id_sketch_stream_columns call at once (no borrow) */
   int32_t reserved[4];     /* must be zero                                      */
@@ -108,7 +108,9 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
 /* Stream ncols snapshot columns (device pointer, column-major, leading
  * dimension ld >= m) into the sketch: W(:, cols) = Psi A(:, cols) and
  * Y += A(:, cols) Omega(cols, :) in ONE read of the columns; the coarse rows
- * A_c(:, cols) are gathered in the same read when want_coarse.
+ * A_c(:, cols) are copied in the same window when want_coarse (FP32 data:
+ * by a second kernel right after the window's sketch, which reads only the
+ * row blocks holding coarse rows).
  * Passage: Sec. 2.1 (snapshots arrive one at a time, the count is not known
  * in advance) and Algorithm 4 step 3 / eq. eq:sampmatrix.
  * Ownership: with window_cols == 0 the columns are read before the call
