@@ -104,6 +104,33 @@ def kernel_traffic(kernel_file, kernel_name):
     return None
 
 
+def pinned_host(shape, how):
+    """A pinned FP32 host tensor: torch's pinned allocator ("torch"), or an
+    anonymous mapping advised for transparent huge pages and registered with
+    CUDA ("thp"), whose pages the copy engines walk in 2 MB steps when the
+    kernel can supply them.  Returns (tensor, handle for release_pinned)."""
+    import torch
+    if how == "torch":
+        return torch.empty(shape, dtype=torch.float32, pin_memory=True), None
+    import mmap
+    import numpy as np
+    nbytes = 4 * int(np.prod(shape))
+    mm = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    mm.madvise(mmap.MADV_HUGEPAGE)
+    arr = np.frombuffer(mm, dtype=np.float32).reshape(shape)
+    t = torch.from_numpy(arr)
+    err = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), nbytes, 0)
+    if int(err) != 0:
+        raise RuntimeError(f"cudaHostRegister failed ({err})")
+    return t, (mm, arr)
+
+
+def release_pinned(t, keep):
+    import torch
+    if keep is not None:
+        torch.cuda.cudart().cudaHostUnregister(t.data_ptr())
+
+
 def gpu_numa_cpus(dev_index):
     """(node, cpus): the host NUMA node sysfs reports for the GPU's PCI device
     and the CPUs of that node this process may run on; None if unknown."""
@@ -384,7 +411,7 @@ def run_ours(args):
         aff = os.sched_getaffinity(0)
         if numa:
             os.sched_setaffinity(0, numa[1])
-        A_host = torch.empty((n, m), dtype=torch.float32, pin_memory=True)
+        A_host, host_keep = pinned_host((n, m), args.host_alloc)
         A_host.copy_(A.T)
         if numa:
             os.sched_setaffinity(0, aff)
@@ -455,7 +482,8 @@ def run_ours(args):
                "ms_per_step": e2e_ms,
                "overlap": "host-to-device copies of step k + 1 under the compute of step k",
                "host_numa_node": numa[0] if numa else None,
-               "h2d_probe_gbs": h2d_probe}
+               "h2d_probe_gbs": h2d_probe, "host_alloc": args.host_alloc}
+        release_pinned(A_host, host_keep)
         del A_host, bufs
 
     cpu = None
@@ -756,6 +784,8 @@ def main():
     ap.add_argument("--prec", choices=["exact", "bf16"], default="exact",
                     help="sketch precision of the channel workload: FP32-accurate (default) "
                          "or the bfloat16 precision form")
+    ap.add_argument("--host-alloc", choices=["torch", "thp"], default="thp",
+                    help="pinned host buffer of the end-to-end run")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="batched workload: the first N problems of the mix (profiling)")
     ap.add_argument("--batch-max-rows", type=int, default=2_000_000,
