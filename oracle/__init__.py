@@ -19,6 +19,9 @@ Modules
                  with its loss, gradients and SGD step, the top-2k proposal,
                  the pivoted QR restricted to it and the fallback rule
                  (import as ``oracle.learned``)
+  fp8            the FP8-E4M3 precision form of the sketch products:
+                 E4M3 rounding, per-column power-of-two scales, the
+                 dequantised matrix (import as ``oracle.fp8``)
 
 Parity status of each function is pinned by ``tests/test_oracle_*.py``; none
 is unpinned.
