@@ -500,11 +500,14 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.prec == "exact" else "bf16",
+                "dtype": {"exact": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[args.prec],
                 "data": "synthetic channel field (seeded), resident in HBM",
-                "config": dict(cfgd, sketch_precision=("FP32-accurate (two bfloat16 pieces)"
-                                                       if args.prec == "exact" else
-                                                       "bfloat16 products, FP32 accumulation")),
+                "config": dict(cfgd, sketch_precision={
+                    "exact": "FP32-accurate (two bfloat16 pieces)",
+                    "bf16": "bfloat16 products, FP32 accumulation",
+                    "fp8": "FP8-E4M3 values with per-column power-of-two scales (a scale pass "
+                           "reads each window once more), products on the bfloat16 tensor cores "
+                           "(E4M3 values are exact there), FP32 accumulation"}[args.prec]),
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "cpu_baseline": cpu,
                 "errors": {"rel_fro": result.get("fro"), "rel_max": result.get("rel_max"),
@@ -781,9 +784,9 @@ def main():
                     default="channel",
                     help="batched64: the batched form (64 matrices of uneven size); "
                          "learned: the learned skeleton proposal (training + comparison)")
-    ap.add_argument("--prec", choices=["exact", "bf16"], default="exact",
-                    help="sketch precision of the channel workload: FP32-accurate (default) "
-                         "or the bfloat16 precision form")
+    ap.add_argument("--prec", choices=["exact", "bf16", "fp8"], default="exact",
+                    help="sketch precision of the channel workload: FP32-accurate (default), "
+                         "the bfloat16 or the FP8-E4M3 precision form")
     ap.add_argument("--host-alloc", choices=["torch", "thp"], default="thp",
                     help="pinned host buffer of the end-to-end run")
     ap.add_argument("--batch-count", type=int, default=64,

@@ -53,10 +53,20 @@ typedef enum {
 typedef enum { ID_F32 = 0, ID_F64 = 1 } id_dtype;
 
 /* Arithmetic of the sketch products W = Psi A and Y = A Omega.
- *   ID_SKETCH_EXACT: FP32-accurate (FP32 data) or FP64 (FP64 data) products.
- *   ID_SKETCH_BF16:  A rounded to bfloat16 once, FP32 accumulation.
- * The pivoted QR and the solve for P are FP64 in every mode. */
-typedef enum { ID_SKETCH_EXACT = 0, ID_SKETCH_BF16 = 1 } id_sketch_prec;
+ *   ID_SKETCH_EXACT:   FP32-accurate (FP32 data) or FP64 (FP64 data) products.
+ *   ID_SKETCH_BF16:    A rounded to bfloat16 once, FP32 accumulation.
+ *   ID_SKETCH_FP8E4M3: FP32 data only, tensor-core path only.  Each column c
+ *                      of a window is scaled by the power of two 2^e_c that
+ *                      brings its largest magnitude closest to 448 without
+ *                      passing it (e_c in [-100, 100], 0 for a zero column;
+ *                      a scale pass reads the window once more), its entries
+ *                      are rounded to FP8-E4M3 (nearest, ties to even), and
+ *                      the products of the dequantised values with Psi and
+ *                      Omega are accumulated in FP32 (the E4M3 values enter
+ *                      the tensor cores exactly as bfloat16).
+ * The pivoted QR and the solve for P are FP64 in every mode; A_c keeps the
+ * data's own values. */
+typedef enum { ID_SKETCH_EXACT = 0, ID_SKETCH_BF16 = 1, ID_SKETCH_FP8E4M3 = 2 } id_sketch_prec;
 
 /* Rank tolerance of the pivoted QR: pivoting stops when every residual
  * column norm is <= ID_RANK_TOL_FACTOR * DBL_EPSILON * ||B||_F, B being the

@@ -24,6 +24,7 @@ ID_F32 = 0
 ID_F64 = 1
 ID_SKETCH_EXACT = 0
 ID_SKETCH_BF16 = 1
+ID_SKETCH_FP8E4M3 = 2
 ID_RANK_TOL_FACTOR = 64.0
 ID_NOALLOC_MAX_KN = 131072
 

@@ -49,7 +49,8 @@ class IdSketch:
         cfg = B.IdConfig()
         cfg.m, cfg.n_max, cfg.k, cfg.l, cfg.seed = m, n_max, k, l, seed
         cfg.dtype = B.ID_F64 if dtype == torch.float64 else B.ID_F32
-        cfg.prec = B.ID_SKETCH_BF16 if prec == "bf16" else B.ID_SKETCH_EXACT
+        cfg.prec = {"exact": B.ID_SKETCH_EXACT, "bf16": B.ID_SKETCH_BF16,
+                    "fp8": B.ID_SKETCH_FP8E4M3}[prec]
         if grid is not None:
             cfg.grid[:] = list(grid)
         cfg.ncomp = ncomp

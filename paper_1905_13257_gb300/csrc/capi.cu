@@ -91,7 +91,7 @@ void free_all(id_sketch* h) {
                   h->d_colpos, h->d_kout, h->d_V, h->d_F, h->d_nu2, h->d_nu20, h->d_gvec, h->d_hvec, h->d_vh, h->d_vl,
                   h->d_upart, h->d_cscal, h->d_cint, h->d_rlist, h->d_Rc, h->d_Pc, h->d_Jc,
                   h->d_colposc, h->d_part, h->d_out3, h->d_Jin, h->d_Pin, h->d_status, h->d_wpart,
-                  h->d_axis, h->d_Sc, h->d_cand, h->d_fq, h->d_crow};
+                  h->d_axis, h->d_Sc, h->d_cand, h->d_fq, h->d_crow, h->d_colscale};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -105,8 +105,9 @@ id_status validate(const id_config* c) {
   if (c->l > kLMax && (c->dtype != ID_F32 || c->want_Y)) return ID_ERR_UNSUPPORTED;
   if (c->want_coarse && c->k > kLMax) return ID_ERR_UNSUPPORTED;
   if (c->dtype != ID_F32 && c->dtype != ID_F64) return ID_ERR_INVALID_ARG;
-  if (c->prec != ID_SKETCH_EXACT && c->prec != ID_SKETCH_BF16) return ID_ERR_INVALID_ARG;
-  if (c->prec == ID_SKETCH_BF16 && c->dtype != ID_F32) return ID_ERR_INVALID_ARG;
+  if (c->prec != ID_SKETCH_EXACT && c->prec != ID_SKETCH_BF16 && c->prec != ID_SKETCH_FP8E4M3)
+    return ID_ERR_INVALID_ARG;
+  if (c->prec != ID_SKETCH_EXACT && c->dtype != ID_F32) return ID_ERR_INVALID_ARG;
   if (c->window_cols < 0) return ID_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (c->reserved[i] != 0) return ID_ERR_INVALID_ARG;
@@ -168,6 +169,8 @@ id_status launch_pending(id_sketch* h) {
     w.col_base = h->n_launched;
     const bool tc = use_tc(h);
     if (!tc && h->l > kLMax) return ID_ERR_UNSUPPORTED;   // wide sketches: tensor-core path only
+    const bool fp8 = h->cfg.prec == ID_SKETCH_FP8E4M3;
+    if (!tc && fp8) return ID_ERR_UNSUPPORTED;             // FP8 form: tensor-core path only
     const int wmax = tc ? kTcMaxTiles * 128 : kSimtWindowMax;
     int taken = 0;
     size_t consumed = 0;
@@ -208,9 +211,13 @@ id_status launch_pending(id_sketch* h) {
     a.bf16 = h->cfg.prec == ID_SKETCH_BF16 ? 1 : 0;
     a.wpart = h->d_wpart;
     a.crow = h->d_crow;
+    a.fp8 = fp8 ? 1 : 0;
+    a.colscale = fp8 ? h->d_colscale + w.col_base : nullptr;
+    if (fp8) IDSK_CUDA(h, launch_fp8_scales(w, h->m, h->d_colscale + w.col_base, h->st));
     const int nsm_eff = h->grid_cap > 0 ? std::min(h->grid_cap, h->nsm) : h->nsm;
     if (tc) {
-      IDSK_CUDA(h, launch_sketch_tc(a, w, a.bf16 ? 1 : 2, nsm_eff, h->drain_blocks, h->d_status,
+      IDSK_CUDA(h, launch_sketch_tc(a, w, (a.bf16 || a.fp8) ? 1 : 2, nsm_eff, h->drain_blocks,
+                                    h->d_status,
                                     h->st, h->timer_sketch));
     } else {
       IDSK_CUDA(h, launch_sketch_simt(a, w, h->cfg.dtype, nsm_eff, h->st));
@@ -390,6 +397,7 @@ id_status id_sketch_create(const id_config* cfg, void* cuda_stream, id_sketch** 
   if (cfg->want_Y) al.get((char**)&h->d_Y, (size_t)h->m * l * h->esz);
   if (cfg->want_coarse) al.get((char**)&h->d_Ac, (size_t)h->mc * nm * h->esz);
   if (cfg->want_coarse && cfg->dtype == ID_F32) al.get(&h->d_crow, (size_t)h->mc);
+  if (cfg->prec == ID_SKETCH_FP8E4M3) al.get(&h->d_colscale, (size_t)nm);
   al.get(&h->d_work, (size_t)l * nm);
   al.get(&h->d_R, (size_t)k * nm);
   al.get(&h->d_P, (size_t)k * nm);

@@ -112,6 +112,8 @@ struct SketchArgs {
   int32_t bf16;         // round A to bfloat16 before the products
   float* wpart;         // tensor-core kernel: per-CTA FP32 W^T slabs [nsm][512][w_width]
   const int64_t* crow;  // tensor-core path: fine row of each coarse row (the A_c copy)
+  const float* colscale;   // FP8 form: 2^e_c of each column of the window (window column 0 first)
+  int32_t fp8;             // FP8-E4M3 form (tensor-core path, one bfloat16 piece)
   int32_t s0;           // first row of Psi drawn by this launch (a multiple of 10)
 };
 
@@ -265,6 +267,7 @@ struct id_sketch {
   void* d_Y = nullptr;
   void* d_Ac = nullptr;
   int64_t* d_crow = nullptr;   // fine row of each coarse-grid row (FP32, want_coarse)
+  float* d_colscale = nullptr;  // FP8 form: per-column power-of-two scales (n_max)
 
   std::vector<idsk::Seg> pend;   // borrowed chunks, window-relative col0
   int64_t pend_cols = 0;
@@ -339,6 +342,9 @@ namespace idsk {
 cudaError_t launch_coarse_rows(const CoarseGeom& g, int64_t m, int64_t* crow, cudaStream_t st);
 cudaError_t launch_coarse_gather(const Window& w, const int64_t* crow, int64_t mc, float* Ac,
                                  cudaStream_t st);
+// FP8 form (sketch_tc.cu): the power-of-two scale of each column of the
+// window into scale[0 .. w.ncols - 1] (one read of the window).
+cudaError_t launch_fp8_scales(const Window& w, int64_t m, float* scale, cudaStream_t st);
 cudaError_t launch_gaussian_fill(uint32_t which, uint32_t k0, uint32_t k1, int64_t first,
                                  int64_t count, int width, const float* table, float* out,
                                  cudaStream_t st);

@@ -168,6 +168,23 @@ __device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window
   return y;
 }
 
+// x rounded to the nearest FP8-E4M3 value, ties to even, saturating at
+// +-448: below 2^-6 the subnormal grid of 2^-9 (rintf rounds half to even),
+// above it 3 mantissa bits (round to nearest even on the 20 dropped bits of
+// the FP32 significand).  E4M3 values are exact in bfloat16.
+__device__ __forceinline__ float e4m3_round(float x) {
+  if (fabsf(x) < 0.015625f) return rintf(x * 512.f) * 0.001953125f;
+  uint32_t b = __float_as_uint(x);
+  b = (b + 0x7FFFFu + ((b >> 20) & 1u)) & 0xFFF00000u;
+  const float q = __uint_as_float(b);
+  return fabsf(q) > 448.f ? copysignf(448.f, x) : q;
+}
+
+__device__ __forceinline__ float4 e4m3_scaled(float4 x, float sc) {
+  return make_float4(e4m3_round(x.x * sc), e4m3_round(x.y * sc), e4m3_round(x.z * sc),
+                     e4m3_round(x.w * sc));
+}
+
 // Psi(0 .. l-1, r) of row r into column rl of a K-major Psi tile (zero past
 // the last row), in groups of ten draws: only the ceil(l / 10) groups that
 // hold rows below l are drawn.  The tile's rows from there to LWT - 1 keep
@@ -263,7 +280,7 @@ struct RoleCounters {
 // partials into the FP32 slab `slab` ([nct * 128][64]).  tm: generic address
 // of the window's tensor map (TMA form); w: the window's segments (register
 // form only).
-template <int NP, bool TMA, bool WY>
+template <int NP, bool TMA, bool WY, bool Q8 = false>
 __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* wp, int ncols,
                                              uint64_t tm, int64_t rb_begin,
                                              int nloc, float* slab, int drain_blocks,
@@ -325,10 +342,13 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
           if (!ok) continue;
           const float* raw = reinterpret_cast<const float*>(rawp + st * RAW_BYTES);
           const int cc = 32 * j + cl;              // column inside the tile
+          float sc = 1.f;                          // FP8 form: the column's scale
+          if (Q8 && ct * TCOLS + cc < ncols) sc = a.colscale[ct * TCOLS + cc];
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int rr = 32 * g + rq;
-            const float4 x = *reinterpret_cast<const float4*>(raw + cl * TR + rr);
+            float4 x = *reinterpret_cast<const float4*>(raw + cl * TR + rr);
+            if (Q8) x = e4m3_scaled(x, sc);
             const uint32_t off = swz((uint32_t)cc, (uint32_t)rr, 2048u);
             const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
             st_shared_v2(hi_buf + off, h01, h23);
@@ -398,7 +418,8 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
                           const float4 (&v)[8]) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const float4 x = split_source(a, w, r0, c0 + j, v[j]);
+        float4 x = split_source(a, w, r0, c0 + j, v[j]);
+        if (Q8) x = e4m3_scaled(x, c0 + j < w.ncols ? a.colscale[c0 + j] : 1.f);
         const uint32_t off = swz((uint32_t)(col_off + j), (uint32_t)row_off, 2048u);
         const uint32_t h01 = pack_bf16x2(x.x, x.y), h23 = pack_bf16x2(x.z, x.w);
         st_shared_v2(pbuf + off, h01, h23);
@@ -695,7 +716,7 @@ __device__ __forceinline__ void sketch_roles(const SketchArgs& a, const Window* 
 
 // Omega(window, :) as a K-major bf16 B operand of the Y product, resident
 // for the row range.
-template <bool TMA>
+template <bool TMA, bool Q8>
 __device__ __forceinline__ void fill_omega(const Smem& S, const SketchArgs& a, int ncols,
                                            int64_t col_base) {
   constexpr int NT_ALL = TMA ? NTHREADS_TMA : NTHREADS;
@@ -703,6 +724,7 @@ __device__ __forceinline__ void fill_omega(const Smem& S, const SketchArgs& a, i
     const int s = e % LP, c = e / LP;
     float v = 0.f;
     if (s < a.l && c < ncols) v = a.omega[(col_base + c) * a.l + s];
+    if (Q8 && c < ncols) v /= a.colscale[c];   // a power of two: exact (FP8 form)
     st_shared_u16(S.omega + (uint32_t)(c >> 7) * OMEGA_TILE_BYTES + swz(s, c & 127, 2048u),
                   bf16_bits(v));
   }
@@ -724,7 +746,7 @@ __device__ __forceinline__ void tmem_free_all(uint32_t tmem) {
 
 // One window of one matrix: CTA b takes the contiguous row blocks
 // [nrb b / G, nrb (b + 1) / G) of the G CTAs, its W^T partials into slab b.
-template <int NP, bool TMA, bool WY>
+template <int NP, bool TMA, bool WY, bool Q8>
 __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     sketch_tc_kernel(const __grid_constant__ SketchArgs a, const __grid_constant__ Window w,
                      int drain_blocks, int* __restrict__ status,
@@ -739,7 +761,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
     st_volatile_shared(S.abort_flag, 0);
     init_bars<TMA>(S);
   }
-  if (WY) fill_omega<TMA>(S, a, w.ncols, w.col_base);
+  if (WY) fill_omega<TMA, Q8>(S, a, w.ncols, w.col_base);
   if (warp == MMA_WARP) tmem_alloc_all(S);
   fence_proxy_async();
   tc_fence_before();
@@ -748,7 +770,7 @@ __global__ void __launch_bounds__(TMA ? NTHREADS_TMA : NTHREADS, 1)
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(S.tmem_slot) : "memory");
   RoleCounters rc;
-  sketch_roles<NP, TMA, WY>(a, &w, w.ncols, reinterpret_cast<uint64_t>(&tmap), rb_begin,
+  sketch_roles<NP, TMA, WY, Q8>(a, &w, w.ncols, reinterpret_cast<uint64_t>(&tmap), rb_begin,
                             (int)(rb_end - rb_begin),
                             a.wpart + (int64_t)blockIdx.x * (kTcMaxTiles * TCOLS) *
                                           w_width(a.l, a.want_Y != 0),
@@ -897,7 +919,7 @@ __global__ void __launch_bounds__(NTHREADS_TMA, 1)
 // (only possible when there are fewer row blocks than CTAs).
 __global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, int l, int lw,
                                     int ncols, int64_t nrb, double* __restrict__ W, int64_t ldw,
-                                    int64_t col_base) {
+                                    int64_t col_base, const float* __restrict__ colscale) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= l * ncols) return;
   const int c = e / l, s = e - c * l;
@@ -916,7 +938,38 @@ __global__ void wpart_reduce_kernel(const float* __restrict__ wpart, int nslab, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) df_add(hi, lo, x[q], 0.f);
   }
-  W[(int64_t)s * ldw + col_base + c] = (double)hi + (double)lo;
+  double wv = (double)hi + (double)lo;
+  if (colscale) wv /= (double)colscale[c];   // FP8 form: a power of two, exact
+  W[(int64_t)s * ldw + col_base + c] = wv;
+}
+
+// FP8 form: per column of the window, the power of two 2^e with
+// max_r |A(r, c)| 2^e <= 448 < max_r |A(r, c)| 2^(e + 1) (e in [-100, 100];
+// 1 for a zero column), into scale[c].  One CTA per column.
+__global__ void fp8_scale_kernel(const __grid_constant__ Window w, int64_t m,
+                                 float* __restrict__ scale) {
+  __shared__ float red[32];
+  const int c = blockIdx.x;
+  const float* col = column_ptr(w, c);
+  float mx = 0.f;
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) mx = fmaxf(mx, fabsf(col[r]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, red[i]);
+    int e = 0;
+    if (mx > 0.f) {
+      int p = 0;
+      const float f = frexpf(mx, &p);   // mx = f 2^p, 0.5 <= f < 1
+      e = f <= 0.875f ? 9 - p : 8 - p;
+      while (e > -100 && ldexpf(mx, e) > 448.f) --e;
+      while (e < 100 && ldexpf(mx, e + 1) <= 448.f) ++e;
+      e = max(-100, min(100, e));
+    }
+    scale[c] = ldexpf(1.f, e);
+  }
 }
 
 template <int NP, bool TMA>
@@ -934,16 +987,16 @@ bool make_tmap(const SketchArgs& a, const Window& w, CUtensorMap* tm) {
   return make_tmap_f32_2d(w.seg[0].ptr, a.m, w.seg[0].ncols, w.seg[0].ld, TR, 32, tm);
 }
 
-template <int NP, bool TMA, bool WY>
+template <int NP, bool TMA, bool WY, bool Q8>
 cudaError_t launch_variant(const SketchArgs& a, const Window& w, int grid, int drain_blocks,
                            int* status, const CUtensorMap& tm, cudaStream_t st,
                            KernelTimer* timer) {
   const size_t sm = tc_smem_bytes<NP, TMA>();
-  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA, WY>,
+  cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel<NP, TMA, WY, Q8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (timer && (e = timer->mark(st)) != cudaSuccess) return e;
-  sketch_tc_kernel<NP, TMA, WY><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(
+  sketch_tc_kernel<NP, TMA, WY, Q8><<<grid, TMA ? NTHREADS_TMA : NTHREADS, sm, st>>>(
       a, w, drain_blocks, status, tm);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (timer) e = timer->mark(st);
@@ -994,14 +1047,24 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   const int grid = (int)std::min<int64_t>(nrb, nsm);
   cudaError_t e;
   auto go = [&](auto np, auto tmaf, auto wy) {
-    return launch_variant<decltype(np)::value, decltype(tmaf)::value, decltype(wy)::value>(
+    return launch_variant<decltype(np)::value, decltype(tmaf)::value, decltype(wy)::value,
+                          false>(a, w, grid, drain_blocks, status, tm, st, timer);
+  };
+  auto go8 = [&](auto tmaf, auto wy) {   // FP8 form: one piece, quantised
+    return launch_variant<1, decltype(tmaf)::value, decltype(wy)::value, true>(
         a, w, grid, drain_blocks, status, tm, st, timer);
   };
   using T = std::true_type;
   using F = std::false_type;
   using N1 = std::integral_constant<int, 1>;
   using N2 = std::integral_constant<int, 2>;
-  if (a.want_Y) {
+  if (a.fp8) {
+    if (npieces != 1 || !a.colscale) return cudaErrorInvalidValue;
+    if (a.want_Y)
+      e = tma ? go8(T(), T()) : go8(F(), T());
+    else
+      e = tma ? go8(T(), F()) : go8(F(), F());
+  } else if (a.want_Y) {
     if (npieces == 1)
       e = tma ? go(N1(), T(), T()) : go(N1(), F(), T());
     else
@@ -1015,7 +1078,8 @@ cudaError_t launch_sketch_tc(const SketchArgs& a0, const Window& w, int npieces,
   if (e != cudaSuccess) return e;
   const int tot = a.l * w.ncols;
   wpart_reduce_kernel<<<(tot + 255) / 256, 256, 0, st>>>(
-      a.wpart, grid, a.l, w_width(a.l, a.want_Y != 0), w.ncols, nrb, a.W, a.ldw, w.col_base);
+      a.wpart, grid, a.l, w_width(a.l, a.want_Y != 0), w.ncols, nrb, a.W, a.ldw, w.col_base,
+      a.fp8 ? a.colscale : nullptr);
   count_launches(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.cg.on) e = launch_coarse_gather(w, a.crow, a.cg.mc, reinterpret_cast<float*>(a.Ac), st);
@@ -1047,6 +1111,13 @@ __global__ void coarse_gather_kernel(const __grid_constant__ Window w,
 
 cudaError_t launch_coarse_rows(const CoarseGeom& g, int64_t m, int64_t* crow, cudaStream_t st) {
   coarse_rows_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g, m, crow);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp8_scales(const Window& w, int64_t m, float* scale, cudaStream_t st) {
+  if (w.ncols <= 0) return cudaSuccess;
+  fp8_scale_kernel<<<w.ncols, 256, 0, st>>>(w, m, scale);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -68,7 +68,8 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(m=0), dict(n_max=0), dict(k=0), dict(k=9, l=8),
                                  dict(l=97, k=4), dict(dtype=3), dict(prec=7),
-                                 dict(prec=1, dtype=1), dict(window_cols=-1),
+                                 dict(prec=1, dtype=1), dict(prec=2, dtype=1),
+                                 dict(prec=3), dict(window_cols=-1),
                                  dict(want_coarse=1, ncomp=3, grid=(10, 10, 10),
                                       coarse_stride=(2, 2, 2)),  # 3000 != m
                                  dict(want_coarse=1, ncomp=1, grid=(10, 10, 10),
