@@ -55,6 +55,7 @@
 // TMEM is freed; the host reads the status word and reports ID_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -168,21 +169,21 @@ __device__ __forceinline__ float4 split_source(const SketchArgs& a, const Window
   return y;
 }
 
-// x rounded to the nearest FP8-E4M3 value, ties to even, saturating at
-// +-448: below 2^-6 the subnormal grid of 2^-9 (rintf rounds half to even),
-// above it 3 mantissa bits (round to nearest even on the 20 dropped bits of
-// the FP32 significand).  E4M3 values are exact in bfloat16.
-__device__ __forceinline__ float e4m3_round(float x) {
-  if (fabsf(x) < 0.015625f) return rintf(x * 512.f) * 0.001953125f;
-  uint32_t b = __float_as_uint(x);
-  b = (b + 0x7FFFFu + ((b >> 20) & 1u)) & 0xFFF00000u;
-  const float q = __uint_as_float(b);
-  return fabsf(q) > 448.f ? copysignf(448.f, x) : q;
+// FP8 form: two values rounded to the nearest FP8-E4M3 value, ties to even,
+// saturating at +-448 (the hardware conversion), and widened back exactly
+// through half precision (E4M3 values are exact in half and in bfloat16);
+// lo goes to the low half.
+__device__ __forceinline__ float2 e4m3x2(float lo, float hi) {
+  uint16_t p;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(p) : "f"(hi), "f"(lo));
+  uint32_t h;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h) : "h"(p));
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
 }
 
 __device__ __forceinline__ float4 e4m3_scaled(float4 x, float sc) {
-  return make_float4(e4m3_round(x.x * sc), e4m3_round(x.y * sc), e4m3_round(x.z * sc),
-                     e4m3_round(x.w * sc));
+  const float2 a = e4m3x2(x.x * sc, x.y * sc), b = e4m3x2(x.z * sc, x.w * sc);
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // Psi(0 .. l-1, r) of row r into column rl of a K-major Psi tile (zero past
