@@ -273,7 +273,7 @@ typedef struct {
   int32_t k;         /* target rank, 1 <= k <= min(l, n)                      */
   int32_t l;         /* sketch width, k <= l <= 64 (<= 96 for FP32 data)     */
   int32_t dtype;     /* id_dtype of A                                         */
-  int32_t prec;      /* id_sketch_prec (ID_SKETCH_BF16 for FP32 data only)    */
+  int32_t prec;      /* ID_SKETCH_EXACT or ID_SKETCH_BF16 (FP32 data only)     */
   int32_t reserved;  /* must be zero                                          */
   uint64_t seed;     /* seed of this problem's Psi and Omega                  */
 } id_batch_problem;
